@@ -1,0 +1,420 @@
+"""Seeded synthetic inputs for the stochastic SC-NEVPT2 / SC-MRCI local-estimator path.
+
+This module stands in for the programs that produce the method's inputs in the paper
+(the integral program and the CASSCF / selected-CI solver of the Results section):
+
+* one-electron integrals h1 and Cholesky-built two-electron integrals (pq|rs),
+* an exact CAS-CI ground state of the active space (the reference phi0),
+* core/virtual orbitals made semicanonical (the paper's H_D uses orbitals that
+  diagonalise the core and virtual generalised Fock blocks, Sec. II C),
+* the random perturber coefficients c_l of the sampling function (Eq. 17).
+
+It contains none of the stochastic method's arithmetic (no local energies, no reach-back
+overlaps, no perturber norms).  Both the oracle and the CUDA path take its arrays as plain
+inputs; neither imports the other.
+
+Everything is seeded (numpy PCG64) so a workload is a pure function of its parameters.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "System", "make_system", "workload", "pack_eri", "unpack_eri", "n_labels",
+    "psi_s_coeffs", "cas_strings", "casci", "WORKLOADS",
+]
+
+
+# --------------------------------------------------------------------------- integrals
+
+def make_integrals(n_core: int, n_act: int, n_virt: int, rank: int, seed: int,
+                   offdiag: float = 0.02, chol_sigma: float = 0.012, coulomb=(0.30, 0.45)):
+    """Random real h1 (symmetric) and Cholesky factors L[K] (symmetric n x n each).
+
+    h1 diagonal is drawn sorted inside each block: core U[-2,-1], active U[-0.5,0.5],
+    virtual U[0.5,3.0]; off-diagonal N(0, offdiag).  eri = sum_K L_K (x) L_K is 8-fold
+    symmetric and positive semidefinite as a pair matrix.  The first three factors are
+    diagonal with entries in `coulomb` (a Coulomb-like (pp|qq) > 0 background); the rest
+    are N(0,1) * exp(-|p-q|/4), symmetrised, scaled by chol_sigma (locality in orbital index).
+    """
+    n = n_core + n_act + n_virt
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = np.concatenate([
+        np.sort(rng.uniform(-2.0, -1.0, n_core)),
+        np.sort(rng.uniform(-0.5, 0.5, n_act)),
+        np.sort(rng.uniform(0.5, 3.0, n_virt)),
+    ])
+    off = rng.normal(0.0, offdiag, (n, n))
+    h1 = 0.5 * (off + off.T)
+    h1[np.diag_indices(n)] = d
+    idx = np.arange(n)
+    decay = np.exp(-np.abs(idx[:, None] - idx[None, :]) / 4.0)
+    L = np.zeros((rank, n, n))
+    for K in range(rank):
+        if K < 3:
+            L[K][np.diag_indices(n)] = rng.uniform(coulomb[0], coulomb[1], n)
+        else:
+            A = rng.normal(0.0, 1.0, (n, n)) * decay
+            L[K] = chol_sigma * 0.5 * (A + A.T)
+    return h1, L
+
+
+def pair_index(p: int, q: int) -> int:
+    """Compound index of an unordered orbital pair, p >= q -> p(p+1)/2 + q."""
+    if p < q:
+        p, q = q, p
+    return p * (p + 1) // 2 + q
+
+
+def pack_eri(L: np.ndarray) -> np.ndarray:
+    """8-fold packed chemists' integrals: eri[P(P1,P2)] = (pq|rs), P1 = P(p,q) >= P2 = P(r,s)."""
+    rank, n, _ = L.shape
+    rows, cols = np.tril_indices(n)            # p >= q, row-major over p: P = p(p+1)/2 + q
+    Lp = L[:, rows, cols]                      # (rank, npair)
+    M = Lp.T @ Lp                              # (npair, npair)
+    r2, c2 = np.tril_indices(M.shape[0])
+    return np.ascontiguousarray(M[r2, c2])
+
+
+def unpack_eri(eri: np.ndarray, n: int) -> np.ndarray:
+    """Full 4-index (pq|rs) array from the packed form (small n only)."""
+    npair = n * (n + 1) // 2
+    M = np.zeros((npair, npair))
+    r2, c2 = np.tril_indices(npair)
+    M[r2, c2] = eri
+    M[c2, r2] = eri
+    out = np.zeros((n, n, n, n))
+    rows, cols = np.tril_indices(n)
+    for P in range(npair):
+        p, q = rows[P], cols[P]
+        blk = np.zeros((n, n))
+        blk[rows, cols] = M[P]
+        blk[cols, rows] = M[P]
+        out[p, q] = blk
+        out[q, p] = blk
+    return out
+
+
+# --------------------------------------------------------------------------- CAS-CI
+
+def cas_strings(norb: int, nel: int) -> np.ndarray:
+    """Occupation strings (bit masks) of nel electrons in norb orbitals, lexicographic order."""
+    return np.array([sum(1 << i for i in c) for c in itertools.combinations(range(norb), nel)],
+                    dtype=np.int64)
+
+
+def _replacement_tables(strs: np.ndarray, norb: int):
+    """E_tu = a+_t a_u on a string space: {(t,u): (src, dst, sign)}; sign from the
+    number of occupied orbitals the operators pass (orbitals ordered ascending)."""
+    index = {int(s): i for i, s in enumerate(strs)}
+    tabs = {}
+    for t in range(norb):
+        for u in range(norb):
+            src, dst, sgn = [], [], []
+            for I, s in enumerate(strs):
+                s = int(s)
+                if not (s >> u) & 1:
+                    continue
+                s1 = s & ~(1 << u)
+                ph = bin(s1 & ((1 << u) - 1)).count("1")
+                if (s1 >> t) & 1:
+                    continue
+                ph += bin(s1 & ((1 << t) - 1)).count("1")
+                s2 = s1 | (1 << t)
+                src.append(I)
+                dst.append(index[s2])
+                sgn.append(-1.0 if ph & 1 else 1.0)
+            tabs[(t, u)] = (np.array(src, dtype=np.int64), np.array(dst, dtype=np.int64),
+                            np.array(sgn))
+    return tabs
+
+
+def _active_hamiltonian(h1, L, n_core, n_act, e_nuc):
+    """Core-averaged active-space Hamiltonian: (E_core, h_eff[t,u], (tu|vw))."""
+    c = slice(0, n_core)
+    a = slice(n_core, n_core + n_act)
+    trLc = np.einsum("kii->k", L[:, c, c])
+    Jc = np.einsum("k,kpq->pq", trLc, L)                       # sum_i (pq|ii)
+    Kc = np.einsum("kpi,kiq->pq", L[:, :, c], L[:, c, :])      # sum_i (pi|iq)
+    e_core = e_nuc + 2.0 * np.trace(h1[c, c]) + 2.0 * np.trace(Jc[c, c]) - np.trace(Kc[c, c])
+    heff = h1[a, a] + 2.0 * Jc[a, a] - Kc[a, a]
+    La = L[:, a, a]
+    eri_a = np.einsum("kpq,krs->pqrs", La, La)
+    return e_core, heff, eri_a
+
+
+class _CasSolver:
+    """String-driven sigma vector for the active-space Hamiltonian
+    H0 = E_core + sum_tu k_tu E_tu + 1/2 sum_tuvw (tu|vw) E_tu E_vw,
+    k_tu = heff_tu - 1/2 sum_v (tv|vu); CI vector stored as C[I_alpha, I_beta]."""
+
+    def __init__(self, e_core, heff, eri_a, na, nb):
+        self.n = n = heff.shape[0]
+        self.e_core = e_core
+        self.heff = heff
+        self.eri = eri_a
+        self.k = heff - 0.5 * np.einsum("tvvu->tu", eri_a)
+        self.sa = cas_strings(n, na)
+        self.sb = cas_strings(n, nb)
+        self.ta = _replacement_tables(self.sa, n)
+        self.tb = self.ta if na == nb else _replacement_tables(self.sb, n)
+        self.shape = (len(self.sa), len(self.sb))
+
+    def _Ea(self, t, u, X):
+        src, dst, sg = self.ta[(t, u)]
+        out = np.zeros_like(X)
+        out[dst] = sg[:, None] * X[src]
+        return out
+
+    def _Eb(self, t, u, X):
+        src, dst, sg = self.tb[(t, u)]
+        out = np.zeros_like(X)
+        out[:, dst] = sg[None, :] * X[:, src]
+        return out
+
+    def E(self, t, u, X):
+        return self._Ea(t, u, X) + self._Eb(t, u, X)
+
+    def sigma(self, C):
+        n = self.n
+        D = np.empty((n, n) + C.shape)
+        for t in range(n):
+            for u in range(n):
+                D[t, u] = self.E(t, u, C)
+        G = np.tensordot(self.eri, D, axes=([2, 3], [0, 1]))
+        S = self.e_core * C + np.tensordot(self.k, D, axes=([0, 1], [0, 1]))
+        for t in range(n):
+            for u in range(n):
+                S += 0.5 * self.E(t, u, G[t, u])
+        return S
+
+    def diagonal(self):
+        n = self.n
+        oa = np.array([[(s >> t) & 1 for t in range(n)] for s in self.sa], dtype=float)
+        ob = np.array([[(s >> t) & 1 for t in range(n)] for s in self.sb], dtype=float)
+        J = np.einsum("ttuu->tu", self.eri)
+        K = np.einsum("tuut->tu", self.eri)
+        hd = np.diag(self.heff)
+        one = (oa @ hd)[:, None] + (ob @ hd)[None, :]
+        tot = oa[:, None, :] + ob[None, :, :]
+        coul = 0.5 * np.einsum("abt,tu,abu->ab", tot, J, tot)
+        exa = 0.5 * np.einsum("at,tu,au->a", oa, K, oa)
+        exb = 0.5 * np.einsum("bt,tu,bu->b", ob, K, ob)
+        return self.e_core + one + coul - exa[:, None] - exb[None, :]
+
+    def rdm1(self, C):
+        n = self.n
+        nrm = np.vdot(C, C)
+        g = np.zeros((n, n))
+        for t in range(n):
+            for u in range(n):
+                g[t, u] = np.vdot(C, self.E(t, u, C)) / nrm
+        return g
+
+
+def _davidson(matvec, diag, x0, tol=1e-11, max_sub=40, max_iter=400):
+    x = x0 / np.linalg.norm(x0)
+    V = [x]
+    AV = [matvec(x)]
+    e = None
+    for _ in range(max_iter):
+        Vm = np.array([v.ravel() for v in V])
+        AVm = np.array([v.ravel() for v in AV])
+        Hs = Vm @ AVm.T
+        Hs = 0.5 * (Hs + Hs.T)
+        w, U = np.linalg.eigh(Hs)
+        e = w[0]
+        x = (U[:, 0] @ Vm).reshape(x0.shape)
+        ax = (U[:, 0] @ AVm).reshape(x0.shape)
+        r = ax - e * x
+        if np.linalg.norm(r) < tol:
+            break
+        den = diag - e
+        den[np.abs(den) < 1e-8] = 1e-8
+        t = -r / den
+        if len(V) >= max_sub:
+            V, AV = [x], [ax]
+        for v in V:
+            t -= np.vdot(v, t) * v
+        for v in V:
+            t -= np.vdot(v, t) * v
+        nt = np.linalg.norm(t)
+        if nt < 1e-14:
+            break
+        t /= nt
+        V.append(t)
+        AV.append(matvec(t))
+    return e, x / np.linalg.norm(x)
+
+
+def casci(h1, L, n_core, n_act, na, nb, e_nuc=0.0):
+    """Exact lowest Sz-conserving eigenpair of the core-averaged active-space Hamiltonian.
+
+    Returns (energy, C[I_alpha, I_beta], alpha strings, beta strings, gamma (spin-summed 1-RDM)).
+    """
+    e_core, heff, eri_a = _active_hamiltonian(h1, L, n_core, n_act, e_nuc)
+    if n_act == 0:
+        C = np.ones((1, 1))
+        return e_core, C, np.zeros(1, np.int64), np.zeros(1, np.int64), np.zeros((0, 0))
+    s = _CasSolver(e_core, heff, eri_a, na, nb)
+    diag = s.diagonal()
+    if diag.size <= 400:
+        # small spaces: dense diagonalisation of the explicit matrix
+        N = diag.size
+        Hm = np.zeros((N, N))
+        for j in range(N):
+            ej = np.zeros(N)
+            ej[j] = 1.0
+            Hm[:, j] = s.sigma(ej.reshape(s.shape)).ravel()
+        w, U = np.linalg.eigh(0.5 * (Hm + Hm.T))
+        e, C = w[0], U[:, 0].reshape(s.shape)
+    else:
+        x0 = np.zeros(s.shape)
+        x0.flat[np.argmin(diag)] = 1.0
+        x0 += 1e-3 * np.random.Generator(np.random.PCG64(7)).normal(size=s.shape)
+        e, C = _davidson(s.sigma, diag, x0)
+    if C.flat[np.argmax(np.abs(C))] < 0:
+        C = -C
+    return e, C, s.sa, s.sb, s.rdm1(C)
+
+
+# --------------------------------------------------------------------------- semicanonical
+
+def _generalized_fock(h1, L, n_core, n_act, gamma):
+    """F_pq = h_pq + sum_i [2(pq|ii) - (pi|iq)] + sum_tu gamma_tu [(pq|tu) - 1/2 (pt|uq)]."""
+    c = slice(0, n_core)
+    a = slice(n_core, n_core + n_act)
+    trLc = np.einsum("kii->k", L[:, c, c])
+    F = h1 + 2.0 * np.einsum("k,kpq->pq", trLc, L) - np.einsum("kpi,kiq->pq", L[:, :, c], L[:, c, :])
+    if n_act:
+        gL = np.einsum("tu,ktu->k", gamma, L[:, a, a])
+        F += np.einsum("k,kpq->pq", gL, L)
+        F -= 0.5 * np.einsum("kpt,tu,kuq->pq", L[:, :, a], gamma, L[:, a, :])
+    return F
+
+
+def semicanonicalize(h1, L, n_core, n_act, gamma):
+    """Rotate core and virtual orbitals to diagonalise their generalised-Fock blocks.
+    Core rotations leave the core density, and virtual rotations the active space, unchanged,
+    so the CAS-CI vector is unchanged."""
+    n = h1.shape[0]
+    F = _generalized_fock(h1, L, n_core, n_act, gamma)
+    U = np.eye(n)
+    c = slice(0, n_core)
+    v = slice(n_core + n_act, n)
+    if n_core:
+        _, U[c, c] = np.linalg.eigh(F[c, c])
+    if n - n_core - n_act:
+        _, U[v, v] = np.linalg.eigh(F[v, v])
+    h1r = U.T @ h1 @ U
+    Lr = np.einsum("pi,kpq,qj->kij", U, L, U)
+    return 0.5 * (h1r + h1r.T), Lr
+
+
+# --------------------------------------------------------------------------- system
+
+def n_labels(n_core: int, n_virt: int) -> int:
+    """Number of perturber labels: (core-hole sets of size <= 2) x (virtual-particle sets of size <= 2)."""
+    nh = 1 + 2 * n_core + (2 * n_core) * (2 * n_core - 1) // 2
+    npart = 1 + 2 * n_virt + (2 * n_virt) * (2 * n_virt - 1) // 2
+    return nh * npart
+
+
+def psi_s_coeffs(nl: int, seed: int) -> np.ndarray:
+    """Sampling-function coefficients (Eq. 17): c_0 = 1, c_l = 0.1 (1 + 0.5 u_l), u_l ~ U[0,1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = 0.1 * (1.0 + 0.5 * rng.random(nl))
+    c[0] = 1.0
+    return c
+
+
+@dataclass
+class System:
+    """One synthetic problem in the library's input format."""
+    n_core: int
+    n_act: int
+    n_virt: int
+    n_alpha: int            # total alpha electrons
+    n_beta: int
+    h1: np.ndarray          # (n, n) row-major, symmetric
+    eri: np.ndarray         # 8-fold packed chemists' (pq|rs)
+    e_nuc: float
+    dets: np.ndarray        # (n_det, 2W) uint64: alpha words then beta words, full-orbital bits
+    coeffs: np.ndarray      # (n_det,)
+    e_cas: float            # CAS-CI eigenvalue from the generator's own solver
+    c: np.ndarray           # (n_labels,) sampling coefficients
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_orb(self) -> int:
+        return self.n_core + self.n_act + self.n_virt
+
+    @property
+    def W(self) -> int:
+        return (self.n_orb + 63) // 64
+
+    @property
+    def n_labels(self) -> int:
+        return n_labels(self.n_core, self.n_virt)
+
+
+def _to_dets(C, sa, sb, n_core, n_orb, drop=0.0):
+    W = (n_orb + 63) // 64
+    core = (1 << n_core) - 1
+    ia, ib = np.nonzero(np.abs(C) > drop) if drop > 0 else np.indices(C.shape).reshape(2, -1)
+    dets = np.zeros((len(ia), 2 * W), dtype=np.uint64)
+    coeffs = C[ia, ib].astype(np.float64)
+    for r, (i, j) in enumerate(zip(ia, ib)):
+        fa = core | (int(sa[i]) << n_core)
+        fb = core | (int(sb[j]) << n_core)
+        for w in range(W):
+            dets[r, w] = np.uint64((fa >> (64 * w)) & 0xFFFFFFFFFFFFFFFF)
+            dets[r, W + w] = np.uint64((fb >> (64 * w)) & 0xFFFFFFFFFFFFFFFF)
+    return dets, coeffs
+
+
+def make_system(n_core, n_act, n_virt, n_alpha, n_beta, rank, seed, *, e_nuc=0.0,
+                semicanonical=True, c_seed=None, drop=0.0, **integral_kw) -> System:
+    """Integrals -> CAS-CI reference -> semicanonical core/virtual -> packed inputs."""
+    h1, L = make_integrals(n_core, n_act, n_virt, rank, seed, **integral_kw)
+    na, nb = n_alpha - n_core, n_beta - n_core
+    if not (0 <= na <= n_act and 0 <= nb <= n_act):
+        raise ValueError("electron count does not fit the active space")
+    e, C, sa, sb, gamma = casci(h1, L, n_core, n_act, na, nb, e_nuc)
+    if semicanonical:
+        h1, L = semicanonicalize(h1, L, n_core, n_act, gamma)
+    n = n_core + n_act + n_virt
+    dets, coeffs = _to_dets(C, sa, sb, n_core, n, drop)
+    nl = n_labels(n_core, n_virt)
+    c = psi_s_coeffs(nl, seed + 17 if c_seed is None else c_seed)
+    return System(n_core, n_act, n_virt, n_alpha, n_beta, np.ascontiguousarray(h1), pack_eri(L),
+                  e_nuc, dets, coeffs, float(e), c,
+                  meta=dict(rank=rank, seed=seed, gamma=gamma, L=L))
+
+
+# --------------------------------------------------------------------------- named workloads
+
+WORKLOADS = {
+    # 12 spatial orbitals (2 core, 4 active, 6 virtual), 8 electrons, Sz = 0, Cholesky rank 40,
+    # factor scale 0.06 (a multireference CAS: natural occupations well away from 0 and 2),
+    # reference = exact CAS(4e,4o) ground state (36 determinants)
+    "tiny_12o_cas4": dict(n_core=2, n_act=4, n_virt=6, n_alpha=4, n_beta=4, rank=40, seed=2009,
+                          chol_sigma=0.06),
+    # 56 spatial orbitals (6 core, 10 active, 40 virtual), 22 electrons, Cholesky rank 168,
+    # factor scale 0.05,
+    # reference = exact CAS(10e,10o) ground state (63,504 determinants)
+    "cas10_56o": dict(n_core=6, n_act=10, n_virt=40, n_alpha=11, n_beta=11, rank=168, seed=2109,
+                      chol_sigma=0.05),
+}
+
+_CACHE: dict = {}
+
+
+def workload(name: str) -> System:
+    """The named seeded workload (memoised in-process)."""
+    if name not in _CACHE:
+        _CACHE[name] = make_system(**WORKLOADS[name])
+    return _CACHE[name]
