@@ -1,0 +1,309 @@
+"""Walker-steps/s of the stochastic SC-NEVPT2(s) local-estimator walk on GB300.
+
+One "step" of this benchmark = one walk launch that advances every walker by `--inner`
+continuous-time steps (each: local energy, reach-back overlaps, H_D numerator, rates,
+accumulation, move) followed by the finalize kernels (E^(2) and jackknife errors).  Inputs
+are the seeded synthetic 56-orbital CAS(10e,10o) system (6 core, 10 active, 40 virtual,
+63,504-determinant reference) with 4,096 walkers, FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank walks its own independent walkers (different seeds),
+there is no data-path collective (weak scaling); timing is barrier-bracketed, max over ranks.
+The reference arm times the CPU oracle (the plain C implementation) on this host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cas10_56o"
+METRIC = "walker-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--inner", type=int, default=1, help="walker steps per walk launch")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) > 8 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(system, seconds: float, threads: int):
+    """Walker-steps/s of the plain C oracle's walk on a bounded sample of the same workload."""
+    import oracle as O
+    orc = O.Oracle.from_system(system)
+    nw = max(threads, 1)
+    t0 = time.perf_counter()
+    acc = orc.sample(nw, 1, 0, seed=3, n_groups=1, threads=threads)
+    t1 = time.perf_counter()
+    steps = 1
+    if (t1 - t0) < seconds / 3:
+        steps = max(1, int(seconds / max(t1 - t0, 1e-3)) - 1)
+        t0 = time.perf_counter()
+        acc = orc.sample(nw, steps, 0, seed=3, n_groups=1, threads=threads)
+        t1 = time.perf_counter()
+    ws = nw * steps
+    return ws / (t1 - t0), dict(walkers=nw, steps=steps, seconds=t1 - t0, type_steps=acc["type_steps"].tolist())
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synthetic as S
+    system = S.workload(WORKLOAD)
+    threads = os.cpu_count() or 1
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
+    rates = []
+    meta = None
+    for k in range(args.warmup + args.steps):
+        r, meta = cpu_oracle_rate(system, per_step, threads)
+        if k >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * meta["walkers"] * meta["steps"] / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers_per_step": meta["walkers"], "steps_per_walker": meta["steps"]},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                         "sample": f"{meta['walkers']} walkers x {meta['steps']} steps per timed step"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_1909_06935_gb300 as P
+    import synthetic as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    system = S.workload(WORKLOAD)
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.Context(local)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.load_hamiltonian(system.n_core, system.n_act, system.n_virt, system.n_alpha, system.n_beta, system.h1,
+                         system.eri, system.e_nuc)
+    ctx.load_reference(system.dets, system.coeffs)
+    ctx.set_coeffs(system.c)
+    nw, inner = args.walkers, args.inner
+    seed = 1000 + rank
+    p = ctx.params(nw, args.warmup * inner, burn_in=0, seed=seed, n_groups=16)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+
+    # warm-up
+    ctx.walkers_init(p)
+    res_w = None
+    for _ in range(args.warmup):
+        ctx.walkers_advance(inner)
+        res_w = ctx.finalize()
+        flush.zero_()
+    snap0 = ctx.walkers(nw)[0]
+    # timed region
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = None
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.walkers_advance(inner)
+            res = ctx.finalize()
+            flush.zero_()
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # walk-kernel time of the timed launches (CUDA events recorded by the library on its stream)
+    walk_s = res["seconds"] - (res_w["seconds"] if res_w else 0.0)
+    walk_launches = res["walk_launches"] - (res_w["walk_launches"] if res_w else 0)
+    snap1 = ctx.walkers(nw)[0]
+    units = nw * inner * args.steps
+    value = world * units / (ms / 1e3)
+
+    # algorithmic accesses per walker-step from the counting kernel on walker snapshots
+    locs = [ctx.debug_local(snap)[0] for snap in (snap0, snap1)]
+    acc_per_step = float(np.mean([np.mean(32.0 * (l["n_gathers"] + l["n_probes"])) for l in locs]))
+    cand_per_step = float(np.mean([np.mean(l["n_candidates"]) for l in locs]))
+    nb_per_step = float(np.mean([np.mean(l["n_neighbours"]) for l in locs]))
+
+    launch_s = walk_s / max(walk_launches, 1)
+    bytes_per_launch = acc_per_step * nw * inner
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_per_launch / launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "k_walk", "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_walker_step": acc_per_step, "launch_seconds": launch_s,
+            "launches_timed": int(walk_launches)}
+
+    # end to end through the public API with host buffers (inputs copied in every step)
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        h2d = system.h1.nbytes + system.eri.nbytes + system.dets.nbytes + system.coeffs.nbytes + system.c.nbytes
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+               dict(h1=system.h1, eri=system.eri, dets=system.dets.view(np.int64), co=system.coeffs,
+                    c=system.c).items()}
+        ctx2 = P.Context(local)
+        ctx2.set_stream(stream.cuda_stream)
+        pe = ctx2.params(nw, inner, burn_in=0, seed=seed, n_groups=16)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx2.load_hamiltonian(system.n_core, system.n_act, system.n_virt, system.n_alpha, system.n_beta,
+                                  pin["h1"], pin["eri"], system.e_nuc)
+            ctx2.load_reference(pin["dets"], pin["co"])
+            ctx2.set_coeffs(pin["c"])
+            ctx2.sample(pe)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        import ctypes
+        d2h = ctypes.sizeof(P.Result)
+        e2e = {"value": nw * inner * args.steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        ctx2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, meta = cpu_oracle_rate(system, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"{meta['walkers']} walkers x {meta['steps']} steps of the same workload "
+                         f"({meta['seconds']:.1f} s; class mix {meta['type_steps']})"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "orbitals": "6 core, 10 active, 40 virtual", "electrons": 22,
+                       "reference_dets": int(len(system.coeffs)), "walkers_per_gpu": nw,
+                       "walker_steps_per_launch": inner, "groups": 16, "method": "SC-NEVPT2(s) + E_L",
+                       "l2": "256 MB buffer written between timed steps",
+                       "neighbours_per_walker_step": nb_per_step, "candidates_per_walker_step": cand_per_step,
+                       "class_mix": {P.TYPE_NAMES[t]: int(res["type_steps"][t]) for t in range(P.NTYPES)},
+                       "e2": res["e2"], "e2_sigma": res["e2_sigma"]},
+            "clocks": clk.summary(),
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,        # per step: walk, finalize-labels, finalize-reduce
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * mrq.h - C ABI of the GB300 (sm_103a) local-estimator library for stochastic strongly
+ * contracted SC-NEVPT2(s) and SC-MRCI(s) (Mahajan, Blunt, Sabzevari, Sharma,
+ * arXiv:1909.06935).
+ *
+ * The library owns one CUDA context slot per `mrq_ctx` and keeps everything the walk needs
+ * resident in device memory: integrals, the reference hash table, sampling coefficients,
+ * walker states and accumulators.  All arithmetic is FP64.
+ *
+ * Conventions shared by every call:
+ *  - n = n_core + n_act + n_virt spatial orbitals (n <= 128), ordered core, active, virtual;
+ *    n_core <= 64, n_act <= 32.
+ *  - A determinant is 2W uint64 words, W = ceil(n/64): alpha occupation bits (bit p of word
+ *    p/64 set when spatial orbital p holds an alpha electron), then beta.  Its sign convention
+ *    is |det> = prod_{alpha p ascending} a+_p prod_{beta p ascending} a+_p |vac>.
+ *  - Integrals are chemists' (pq|rs), 8-fold packed: eri[P(P(p,q),P(r,s))],
+ *    P(x,y) = x(x+1)/2 + y for x >= y, so eri has P(P+1)/2 entries with P = n(n+1)/2.
+ *  - The perturber label of a determinant (the subspace S_l^(k) of Sec. II A, read in spin
+ *    orbitals) is its set H of empty core spin orbitals and its set P of occupied virtual spin
+ *    orbitals, |H| <= 2, |P| <= 2: label = rank(H) * nP + rank(P), rank(empty) = 0,
+ *    rank({x}) = 1 + x, rank({x<y}) = 1 + m + y(y-1)/2 + x, where core spin orbital x =
+ *    sigma*n_core + i, virtual spin orbital x = sigma*n_virt + a, m = number of spin orbitals
+ *    of that space, nP = 1 + 2 n_virt + C(2 n_virt, 2).  Label 0 is the CAS.  The number of
+ *    labels is nH * nP, nH = 1 + 2 n_core + C(2 n_core, 2).
+ *  - Its type is 3h + p (h = |H|, p = |P|): 0 CAS, 1 S_r, 2 S_rs, 3 S_i, 4 S_i,r, 5 S_i,rs,
+ *    6 S_ij, 7 S_ij,r, 8 S_ij,rs (NEVPT notation of Angeli et al.).
+ *  - Pointer arguments may address host or device memory (unified addressing decides);
+ *    the library copies inputs in before returning, so the caller keeps ownership.
+ *  - Every call returns 0 or a negative `mrq_status`; `mrq_last_error` gives the message.
+ *    A context must be used by one host thread at a time.
+ */
+#ifndef MRQ_H
+#define MRQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrq_ctx mrq_ctx;
+
+enum mrq_status {
+    MRQ_OK = 0,
+    MRQ_INVALID_ARG = -1,
+    MRQ_NOT_LOADED = -2,
+    MRQ_BAD_REFERENCE = -3,   /* a determinant with a core hole, a virtual electron, the wrong
+                                 electron count, or a duplicate */
+    MRQ_OOM = -4,
+    MRQ_HASH_OVERFLOW = -5,   /* a hash probe ran past its bound */
+    MRQ_DEVICE_TIMEOUT = -6,
+    MRQ_CUDA_ERROR = -7,
+    MRQ_NO_MOVE = -8,         /* a walker found no determinant to move to (all rates zero) */
+    MRQ_TOO_LARGE = -9
+};
+
+enum mrq_method { MRQ_SC_NEVPT2 = 0, MRQ_SC_MRCI = 1 };
+
+#define MRQ_NTYPES 9
+
+/* Sampling parameters. */
+typedef struct {
+    int64_t n_walkers;      /* independent continuous-time walkers (Sec. II B) */
+    int64_t n_steps;        /* steps per walker in this call (including burn-in on a fresh start) */
+    int64_t burn_in;        /* leading steps of every walker left out of the averages */
+    uint64_t seed;          /* Philox4x32-10 key of the move selection */
+    int32_t n_groups;       /* G walker groups for jackknife errors (walker w is in group w mod G) */
+    int32_t method;         /* mrq_method: informative; both estimators are always accumulated */
+    double screen_tau;      /* perturbers with N_l/N_0 below this are screened out (Sec. II C) */
+    int32_t walkers_per_block; /* 0: library default */
+    int32_t reserved;
+} mrq_sample_params;
+
+/* Result of a sampling run (all energies in Hartree). */
+typedef struct {
+    double e0;                      /* <phi0|H|phi0>/<phi0|phi0> */
+    double e2, e2_sigma;            /* SC-NEVPT2 second-order energy (Eq. 15), jackknife sigma */
+    double e_var, e_var_sigma;      /* <E_L> of the sampled function (Eq. 4): SC-MRCI energy for given c */
+    double a0sq, a0sq_sigma;        /* c_0^2 <phi0|phi0>/<psi|psi> (Eq. 11-12) */
+    double e_mrci_q;                /* e_var + (1 - a0sq)(e_var - e0), Davidson +Q (Eq. 10) */
+    double type_norm[MRQ_NTYPES], type_norm_sigma[MRQ_NTYPES];  /* sum of kept N_l/N_0 per type */
+    double type_e2[MRQ_NTYPES], type_e2_sigma[MRQ_NTYPES];      /* E^(2) contribution per type */
+    double type_screened[MRQ_NTYPES];     /* visited labels screened out, per type */
+    double screened_norm;                 /* sum of N_l/N_0 over screened labels */
+    double n_labels_visited;
+    int64_t type_steps[MRQ_NTYPES];       /* walker steps spent at each type (class mix) */
+    int64_t walker_steps;                 /* accumulated (post burn-in) walker steps */
+    int64_t total_steps;                  /* all walker steps taken by this context */
+    double seconds;                       /* device time of the walk kernels since mrq_walkers_init */
+    int64_t walk_launches;                /* walk kernel launches since mrq_walkers_init */
+    int32_t status;
+    int32_t reserved;
+} mrq_result;
+
+/* Per-determinant local quantities (debug / parity; Eq. 5, Eq. 16). */
+typedef struct {
+    double S;         /* sum_m Gamma_nm, Gamma_nm = |H_nm psi_s(m)/psi_s(n)| */
+    double e_local;   /* E_L(n) = sum_m H_nm psi_s(m)/psi_s(n) including m = n (Eq. 5) */
+    double num;       /* sum_m (H_D)_nm psi_s(m)/psi_s(n) over m of n's label (Eq. 16), 0 in the CAS */
+    double h_nn, hd_nn, psi;   /* <n|H|n>, <n|H_D|n>, psi_s(n) */
+    int64_t label;    /* -1 outside CAS and FOIS */
+    int64_t type;
+    int64_t n_neighbours;
+    int64_t n_candidates; /* reach-back candidates tried (hash lookups of neighbours and of their CAS images) */
+    int64_t n_probes;     /* hash slots read (16 B each) */
+    int64_t n_gathers;    /* 8 B random reads of integrals and per-orbital / per-label tables */
+} mrq_local;
+
+/* Per-neighbour record of mrq_debug_local. */
+typedef struct {
+    uint64_t det[4];  /* first 2W words used */
+    double h, hd;     /* <n|H|m>, <n|H_D|m> (0 unless same label and n outside the CAS) */
+    double o;         /* phi0(m) for a CAS m, O(m) = <m|H|phi0> otherwise (Eq. 6-7) */
+    double psi;       /* psi_s(m) */
+    double gamma;     /* |H_nm psi_s(m)/psi_s(n)| */
+    uint32_t exc;     /* removed spin orbitals r1<=r2, added a1<=a2: r1 | r2<<8 | a1<<16 | a2<<24 */
+    uint32_t pad;
+} mrq_neighbour;
+
+/* Create a context on CUDA device `device`.  Returns 0 or a negative status. */
+int mrq_create(mrq_ctx** out, int device);
+
+/* Free everything the context holds (device memory, stream, events).  NULL is ignored. */
+void mrq_destroy(mrq_ctx* ctx);
+
+/* Message of the last failing call on this context ("" when none). Valid until the next call. */
+const char* mrq_last_error(const mrq_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t, or NULL for the context's own stream) for all later work. */
+int mrq_set_stream(mrq_ctx* ctx, void* stream);
+
+/*
+ * Load the Hamiltonian (the problem statement of Sec. II A and the Dyall partition of
+ * Sec. II C): n_core doubly occupied core, n_act active and n_virt virtual spatial orbitals,
+ * n_alpha/n_beta electrons in total, h1 (n*n row-major, symmetric), eri (8-fold packed, see
+ * above) and a constant e_core added to every diagonal element (e.g. nuclear repulsion).
+ * Replaces any previous Hamiltonian and invalidates the reference and walkers.
+ * Errors: MRQ_INVALID_ARG (sizes), MRQ_OOM, MRQ_CUDA_ERROR.
+ */
+int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_alpha, int n_beta,
+                         const double* h1, const double* eri, double e_core);
+
+/*
+ * Load the reference phi0 (Sec. II D: a selected-CI vector kept in a hash table): n_det
+ * determinants (n_det x 2W words) with coefficients (need not be normalised).  Builds the
+ * device hash table and the one-time quantities of Sec. II C: E0 = <phi0|H|phi0>/<phi0|phi0>,
+ * the active 1-RDM, the generalised-Fock diagonal eps, and the core-averaged operators.
+ * Also sets the sampling coefficients to c_0 = 1, c_l = 0.1 for every label (override with
+ * mrq_set_coeffs).  Errors: MRQ_NOT_LOADED (no Hamiltonian), MRQ_BAD_REFERENCE,
+ * MRQ_HASH_OVERFLOW, MRQ_OOM, MRQ_CUDA_ERROR.
+ */
+int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const double* coeffs);
+
+/*
+ * Coefficients c_l of the sampled function psi = c_0 phi0 + sum_l c_l psi_l (Eq. 17 for
+ * SC-NEVPT2(s), the SC-MRCI(s) wave function of Sec. II B for given c), one per label in
+ * label order (see above); n_labels must equal nH * nP.  Errors: MRQ_INVALID_ARG, MRQ_NOT_LOADED.
+ */
+int mrq_set_coeffs(mrq_ctx* ctx, int64_t n_labels, const double* c);
+
+/* Number of labels nH * nP of the loaded Hamiltonian (0 when none). */
+int64_t mrq_n_labels(const mrq_ctx* ctx);
+
+/*
+ * Setup quantities after mrq_load_reference: out[0] = E0, out[1] = <phi0|phi0>, out[2] = E_core
+ * (core energy), out[3] = sum of core eps, out[4] = index (input order) of the largest |c|
+ * determinant (the walkers' start).  eps receives n doubles (or NULL), gamma n_act^2 (or NULL).
+ */
+int mrq_setup_info(mrq_ctx* ctx, double* out5, double* eps, double* gamma);
+
+/*
+ * Local quantities of n determinants (Eq. 5, Eq. 16, Sec. II D), for parity checks: local[i]
+ * for det i; when nb != NULL the neighbours of det i go to nb[i*max_nb ...] (at most max_nb
+ * each, in the library's enumeration order; local[i].n_neighbours gives the full count).
+ */
+int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* local,
+                    int64_t max_nb, mrq_neighbour* nb);
+
+/*
+ * Start n_walkers fresh walkers at the largest-|phi0| determinant and clear the accumulators
+ * (G = n_groups groups).  Errors: MRQ_NOT_LOADED, MRQ_INVALID_ARG, MRQ_OOM.
+ */
+int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p);
+
+/*
+ * Advance every walker by n_steps continuous-time steps (Sec. II B; first-reaction form of
+ * Gillespie's algorithm with Philox4x32-10 clocks keyed on (seed; exc, step, walker)),
+ * accumulating the estimators of Eq. 4, 12 and 16 after each walker's burn-in.  Asynchronous
+ * on the context stream.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
+ */
+int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps);
+
+/*
+ * Finalize the accumulators into `out` (Eq. 14-15 with screening at screen_tau, jackknife
+ * errors over the G groups).  Synchronises the stream; reports device-side error flags
+ * (MRQ_HASH_OVERFLOW, MRQ_NO_MOVE) in the return value and out->status.
+ */
+int mrq_finalize(mrq_ctx* ctx, mrq_result* out);
+
+/* mrq_walkers_init + mrq_walkers_advance(p->n_steps) + mrq_finalize. */
+int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out);
+
+/*
+ * Raw accumulators of the last walk: accN/accU (G x n_labels), accW/accE (G), type_steps (9).
+ * Any pointer may be NULL.  Synchronises the stream.
+ */
+int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW, double* accE,
+                          int64_t* type_steps);
+
+/* Walker determinants (n_walkers x 2W words) and psi_s values; either may be NULL. */
+int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRQ_H */

@@ -1,0 +1,250 @@
+"""GB300-native local-estimator path of stochastic SC-NEVPT2(s) / SC-MRCI(s) (arXiv:1909.06935).
+
+Thin ctypes binding over the C ABI in include/mrq.h (library: _build/libmrq.so, built by
+``build.build()``).  Arguments are marshalled here; every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: loading fails loudly when the library is
+missing or no CUDA device is visible.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Context", "SampleParams", "Result", "Local", "Neighbour", "MRQError", "load_library", "NTYPES",
+           "TYPE_NAMES", "n_labels"]
+
+NTYPES = 9
+TYPE_NAMES = ["CAS", "S_r", "S_rs", "S_i", "S_ir", "S_irs", "S_ij", "S_ijr", "S_ijrs"]   # index 3h + p
+SC_NEVPT2, SC_MRCI = 0, 1
+
+
+class SampleParams(C.Structure):
+    _fields_ = [("n_walkers", C.c_int64), ("n_steps", C.c_int64), ("burn_in", C.c_int64), ("seed", C.c_uint64),
+                ("n_groups", C.c_int32), ("method", C.c_int32), ("screen_tau", C.c_double),
+                ("walkers_per_block", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("e0", C.c_double), ("e2", C.c_double), ("e2_sigma", C.c_double), ("e_var", C.c_double),
+                ("e_var_sigma", C.c_double), ("a0sq", C.c_double), ("a0sq_sigma", C.c_double),
+                ("e_mrci_q", C.c_double),
+                ("type_norm", C.c_double * NTYPES), ("type_norm_sigma", C.c_double * NTYPES),
+                ("type_e2", C.c_double * NTYPES), ("type_e2_sigma", C.c_double * NTYPES),
+                ("type_screened", C.c_double * NTYPES), ("screened_norm", C.c_double),
+                ("n_labels_visited", C.c_double), ("type_steps", C.c_int64 * NTYPES),
+                ("walker_steps", C.c_int64), ("total_steps", C.c_int64), ("seconds", C.c_double),
+                ("walk_launches", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = np.array(v[:]) if hasattr(v, "_length_") else v
+        return out
+
+
+class Local(C.Structure):
+    _fields_ = [("S", C.c_double), ("e_local", C.c_double), ("num", C.c_double), ("h_nn", C.c_double),
+                ("hd_nn", C.c_double), ("psi", C.c_double), ("label", C.c_int64), ("type", C.c_int64),
+                ("n_neighbours", C.c_int64), ("n_candidates", C.c_int64), ("n_probes", C.c_int64),
+                ("n_gathers", C.c_int64)]
+
+
+class Neighbour(C.Structure):
+    _fields_ = [("det", C.c_uint64 * 4), ("h", C.c_double), ("hd", C.c_double), ("o", C.c_double),
+                ("psi", C.c_double), ("gamma", C.c_double), ("exc", C.c_uint32), ("pad", C.c_uint32)]
+
+
+_NB_DTYPE = np.dtype([("det", np.uint64, 4), ("h", np.float64), ("hd", np.float64), ("o", np.float64),
+                      ("psi", np.float64), ("gamma", np.float64), ("exc", np.uint32), ("pad", np.uint32)])
+_LOCAL_DTYPE = np.dtype([("S", np.float64), ("e_local", np.float64), ("num", np.float64), ("h_nn", np.float64),
+                         ("hd_nn", np.float64), ("psi", np.float64), ("label", np.int64), ("type", np.int64),
+                         ("n_neighbours", np.int64), ("n_candidates", np.int64), ("n_probes", np.int64),
+                         ("n_gathers", np.int64)])
+assert _NB_DTYPE.itemsize == C.sizeof(Neighbour) and _LOCAL_DTYPE.itemsize == C.sizeof(Local)
+
+
+class MRQError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mrq error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load _build/libmrq.so (building it with nvcc when missing).  Raises when it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I64 = C.c_void_p, C.c_int64
+    lib.mrq_create.argtypes = [C.POINTER(C.c_void_p), C.c_int]
+    lib.mrq_destroy.argtypes = [P]
+    lib.mrq_destroy.restype = None
+    lib.mrq_last_error.argtypes = [P]
+    lib.mrq_last_error.restype = C.c_char_p
+    lib.mrq_set_stream.argtypes = [P, P]
+    lib.mrq_load_hamiltonian.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_double]
+    lib.mrq_load_reference.argtypes = [P, I64, P, P]
+    lib.mrq_set_coeffs.argtypes = [P, I64, P]
+    lib.mrq_n_labels.argtypes = [P]
+    lib.mrq_n_labels.restype = I64
+    lib.mrq_setup_info.argtypes = [P, P, P, P]
+    lib.mrq_debug_local.argtypes = [P, I64, P, P, I64, P]
+    lib.mrq_walkers_init.argtypes = [P, C.POINTER(SampleParams)]
+    lib.mrq_walkers_advance.argtypes = [P, I64]
+    lib.mrq_finalize.argtypes = [P, C.POINTER(Result)]
+    lib.mrq_sample.argtypes = [P, C.POINTER(SampleParams), C.POINTER(Result)]
+    lib.mrq_read_accumulators.argtypes = [P, P, P, P, P, P]
+    lib.mrq_read_walkers.argtypes = [P, P, P]
+    for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
+               "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
+               "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
+        getattr(lib, fn).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def n_labels(n_core: int, n_virt: int) -> int:
+    nh = 1 + 2 * n_core + (2 * n_core) * (2 * n_core - 1) // 2
+    npart = 1 + 2 * n_virt + (2 * n_virt) * (2 * n_virt - 1) // 2
+    return nh * npart
+
+
+def _addr(a):
+    """Address of a host numpy array or a CUDA torch tensor (unified addressing)."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _host(a, dtype):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """One device-resident system (Hamiltonian, reference, coefficients, walkers)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load_library()
+        h = C.c_void_p()
+        rc = self._lib.mrq_create(C.byref(h), device)
+        if rc:
+            raise MRQError(rc, "mrq_create failed (no CUDA device?)")
+        self._h = h
+        self.W = 1
+        self.n_core = self.n_act = self.n_virt = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mrq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc:
+            raise MRQError(rc, self._lib.mrq_last_error(self._h).decode())
+
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self._lib.mrq_set_stream(self._h, C.c_void_p(stream_ptr or 0)))
+
+    def load_hamiltonian(self, n_core, n_act, n_virt, n_alpha, n_beta, h1, eri, e_core=0.0):
+        h1a, eria = _host(h1, np.float64), _host(eri, np.float64)
+        self._check(self._lib.mrq_load_hamiltonian(self._h, n_core, n_act, n_virt, n_alpha, n_beta, _addr(h1a),
+                                                   _addr(eria), float(e_core)))
+        self.n_core, self.n_act, self.n_virt = n_core, n_act, n_virt
+        self.n = n_core + n_act + n_virt
+        self.W = (self.n + 63) // 64
+
+    def load_reference(self, dets, coeffs):
+        d, c = _host(dets, np.uint64), _host(coeffs, np.float64)
+        self._check(self._lib.mrq_load_reference(self._h, len(c), _addr(d), _addr(c)))
+
+    def set_coeffs(self, c):
+        ca = _host(c, np.float64)
+        self._check(self._lib.mrq_set_coeffs(self._h, len(ca), _addr(ca)))
+
+    @property
+    def n_labels(self) -> int:
+        return int(self._lib.mrq_n_labels(self._h))
+
+    def setup_info(self):
+        out = np.zeros(5)
+        eps = np.zeros(self.n)
+        gam = np.zeros(max(self.n_act, 1) ** 2)
+        self._check(self._lib.mrq_setup_info(self._h, _addr(out), _addr(eps), _addr(gam)))
+        return dict(e0=out[0], norm0=out[1], e_core=out[2], sum_eps_core=out[3], start=int(out[4]), eps=eps,
+                    gamma=gam[: self.n_act ** 2].reshape(self.n_act, self.n_act))
+
+    @classmethod
+    def from_system(cls, s, device: int = 0, c=None):
+        ctx = cls(device)
+        ctx.load_hamiltonian(s.n_core, s.n_act, s.n_virt, s.n_alpha, s.n_beta, s.h1, s.eri, s.e_nuc)
+        ctx.load_reference(s.dets, s.coeffs)
+        ctx.set_coeffs(s.c if c is None else c)
+        return ctx
+
+    def debug_local(self, dets, max_nb: int = 0):
+        d = np.ascontiguousarray(dets, np.uint64).reshape(-1, 2 * self.W)
+        n = d.shape[0]
+        loc = np.zeros(n, _LOCAL_DTYPE)
+        nb = np.zeros(n * max_nb, _NB_DTYPE) if max_nb else None
+        self._check(self._lib.mrq_debug_local(self._h, n, _addr(d), _addr(loc), max_nb,
+                                              _addr(nb) if max_nb else None))
+        return loc, (nb.reshape(n, max_nb) if max_nb else None)
+
+    def params(self, n_walkers, n_steps, burn_in=0, seed=1, n_groups=16, screen_tau=1e-10, method=SC_NEVPT2):
+        return SampleParams(n_walkers, n_steps, burn_in, seed, n_groups, method, screen_tau, 0, 0)
+
+    def walkers_init(self, p: SampleParams):
+        self._check(self._lib.mrq_walkers_init(self._h, C.byref(p)))
+
+    def walkers_advance(self, n_steps: int):
+        self._check(self._lib.mrq_walkers_advance(self._h, n_steps))
+
+    def finalize(self) -> dict:
+        r = Result()
+        self._check(self._lib.mrq_finalize(self._h, C.byref(r)))
+        return r.as_dict()
+
+    def sample(self, p: SampleParams) -> dict:
+        r = Result()
+        self._check(self._lib.mrq_sample(self._h, C.byref(p), C.byref(r)))
+        return r.as_dict()
+
+    def accumulators(self, n_groups: int):
+        L = self.n_labels
+        N = np.zeros((n_groups, L))
+        U = np.zeros((n_groups, L))
+        Wg = np.zeros(n_groups)
+        E = np.zeros(n_groups)
+        ts = np.zeros(NTYPES, np.int64)
+        self._check(self._lib.mrq_read_accumulators(self._h, _addr(N), _addr(U), _addr(Wg), _addr(E), _addr(ts)))
+        return dict(N=N, U=U, W=Wg, E=E, type_steps=ts)
+
+    def walkers(self, n_walkers: int):
+        d = np.zeros((n_walkers, 2 * self.W), np.uint64)
+        psi = np.zeros(n_walkers)
+        self._check(self._lib.mrq_read_walkers(self._h, _addr(d), _addr(psi)))
+        return d, psi

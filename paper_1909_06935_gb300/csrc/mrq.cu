@@ -1,0 +1,1558 @@
+// mrq.cu - GB300 (sm_103a) kernels and host runtime of the stochastic SC-NEVPT2(s) /
+// SC-MRCI(s) local-estimator path (arXiv:1909.06935), behind the C ABI of include/mrq.h.
+//
+// Hot path (one warp per walker, persistent over steps):
+//   classify the walker (label, Sec. II A) -> enumerate every single and double excitation that
+//   stays in CAS u FOIS as a union of rectangular class blocks -> per lane: <n|H|m> by
+//   Slater-Condon, psi_s(m) by a hash probe (m in the CAS) or reach-back O(m) = <m|H|phi0>
+//   (Eq. 6-7, Sec. II D) -> rates Gamma_nm = |H_nm psi_s(m)/psi_s(n)|, E_L (Eq. 5), the H_D
+//   numerator (Eq. 16) -> warp reductions -> accumulate with weight 1/S -> move by the
+//   first-reaction (competing exponential clocks) form of Gillespie's algorithm.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mrq.h"
+#include "mrq_device.cuh"
+
+// ============================================================================ per-warp state
+
+struct Walker {
+    unsigned long long d[2][2];   // [spin][word]
+    double psi;                   // psi_s of the current determinant
+    unsigned step;                // steps taken by this walker so far
+    unsigned wid;                 // walker id (Philox counter word)
+    int sys;                      // index into the system table
+    int group;                    // accumulator group
+};
+
+struct WarpSh {
+    unsigned char ol[2][MRQ_MAXN];   // occupied orbitals per spin, ascending (core|active|virtual)
+    unsigned char el[2][MRQ_MAXN];   // empty orbitals per spin
+    short os[2][4], es[2][4];        // class starts: [spin][class], [3] = count
+    int bstart[MRQ_MAXB + 1];        // block prefix offsets
+    unsigned bdesc[MRQ_MAXB];        // block descriptors
+    int nb;
+};
+
+// pair tables for same-spin doubles: (X1, X2) with X1 <= X2
+__constant__ unsigned char c_pair_a[6] = {0, 0, 0, 1, 1, 2};
+__constant__ unsigned char c_pair_b[6] = {0, 1, 2, 1, 2, 2};
+
+__device__ __forceinline__ int pairs_of(int k1, int k2, bool same) { return same ? k1 * (k1 - 1) / 2 : k1 * k2; }
+
+// decode a pair index inside one class (triangular, i < j) or across two classes
+__device__ __forceinline__ void tri_decode(int op, int& i, int& j) {
+    int jj = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)op)) * 0.5f);
+    while (jj * (jj - 1) / 2 > op) jj--;
+    while ((jj + 1) * jj / 2 <= op) jj++;
+    j = jj;
+    i = op - jj * (jj - 1) / 2;
+}
+
+// Build occupied/empty lists (class-partitioned) and the valid excitation blocks of det d.
+template <int W>
+__device__ void build_lists(const SysDev& S, const unsigned long long (&d)[2][W], WarpSh& sh, int h, int p,
+                            int lane) {
+    const int n = S.n;
+    for (int sg = 0; sg < 2; sg++) {
+        int no = 0, ne = 0;
+        for (int base = 0; base < n; base += 32) {
+            int q = base + lane;
+            bool valid = q < n;
+            bool o = valid && bit_of<W>(d[sg], q);
+            unsigned bo = __ballot_sync(0xffffffffu, o);
+            unsigned be = __ballot_sync(0xffffffffu, valid && !o);
+            unsigned lt = (1u << lane) - 1u;
+            if (o) sh.ol[sg][no + __popc(bo & lt)] = (unsigned char)q;
+            if (valid && !o) sh.el[sg][ne + __popc(be & lt)] = (unsigned char)q;
+            no += __popc(bo);
+            ne += __popc(be);
+        }
+        if (lane == 0) {
+            int oc = 0, oa = 0, ov = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                oc += __popcll(d[sg][w] & S.mcore[w]);
+                oa += __popcll(d[sg][w] & S.mact[w]);
+                ov += __popcll(d[sg][w] & S.mvirt[w]);
+            }
+            sh.os[sg][0] = 0;
+            sh.os[sg][1] = oc;
+            sh.os[sg][2] = oc + oa;
+            sh.os[sg][3] = oc + oa + ov;
+            sh.es[sg][0] = 0;
+            sh.es[sg][1] = S.nc - oc;
+            sh.es[sg][2] = S.nc - oc + S.na - oa;
+            sh.es[sg][3] = n - (oc + oa + ov);
+        }
+    }
+    __syncwarp();
+    // candidate blocks: 18 singles, 72 same-spin doubles, 81 opposite-spin doubles
+    int run = 0, carry = 0;
+    for (int base = 0; base < MRQ_MAXB; base += 32) {
+        int ci = base + lane;
+        int size = 0, kind = 0, sg = 0, X1 = 0, X2 = 0, Y1 = 0, Y2 = 0;
+        if (ci < MRQ_MAXB) {
+            if (ci < 18) {
+                kind = 0; sg = ci / 9; X1 = (ci % 9) / 3; Y1 = ci % 3;
+                size = (sh.os[sg][X1 + 1] - sh.os[sg][X1]) * (sh.es[sg][Y1 + 1] - sh.es[sg][Y1]);
+            } else if (ci < 90) {
+                int c = ci - 18;
+                kind = 1; sg = c / 36;
+                int px = (c % 36) / 6, py = c % 6;
+                X1 = c_pair_a[px]; X2 = c_pair_b[px]; Y1 = c_pair_a[py]; Y2 = c_pair_b[py];
+                int k1 = sh.os[sg][X1 + 1] - sh.os[sg][X1], k2 = sh.os[sg][X2 + 1] - sh.os[sg][X2];
+                int e1 = sh.es[sg][Y1 + 1] - sh.es[sg][Y1], e2 = sh.es[sg][Y2 + 1] - sh.es[sg][Y2];
+                size = pairs_of(k1, k2, X1 == X2) * pairs_of(e1, e2, Y1 == Y2);
+            } else {
+                int c = ci - 90;
+                kind = 2; X1 = c / 27; Y1 = (c / 9) % 3; X2 = (c / 3) % 3; Y2 = c % 3;
+                size = (sh.os[0][X1 + 1] - sh.os[0][X1]) * (sh.es[0][Y1 + 1] - sh.es[0][Y1]) *
+                       (sh.os[1][X2 + 1] - sh.os[1][X2]) * (sh.es[1][Y2 + 1] - sh.es[1][Y2]);
+            }
+            int dh = (X1 == 0) - (Y1 == 0), dp = (Y1 == 2) - (X1 == 2);
+            if (kind != 0) {
+                dh += (X2 == 0) - (Y2 == 0);
+                dp += (Y2 == 2) - (X2 == 2);
+            }
+            if (h + dh > 2 || p + dp > 2) size = 0;
+        }
+        unsigned vm = __ballot_sync(0xffffffffu, size > 0);
+        // inclusive scan of sizes (invalid lanes contribute 0) -> global prefix via the carry
+        int x = size;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (size > 0) {
+            int k = run + __popc(vm & ((1u << lane) - 1u));
+            sh.bdesc[k] = (unsigned)kind | ((unsigned)sg << 2) | ((unsigned)X1 << 4) | ((unsigned)X2 << 6) |
+                          ((unsigned)Y1 << 8) | ((unsigned)Y2 << 10);
+            sh.bstart[k + 1] = carry + x;
+        }
+        carry += __shfl_sync(0xffffffffu, x, 31);
+        run += __popc(vm);
+    }
+    if (lane == 0) {
+        sh.nb = run;
+        sh.bstart[0] = 0;
+    }
+    __syncwarp();
+}
+
+// decode neighbour `loc` of block `desc` into removed r1<=r2 and added a1<=a2 spin orbitals
+__device__ __forceinline__ void decode_exc(const WarpSh& sh, int n, unsigned desc, int loc, int& kind, int& r1,
+                                           int& r2, int& a1, int& a2) {
+    kind = desc & 3;
+    int sg = (desc >> 2) & 1, X1 = (desc >> 4) & 3, X2 = (desc >> 6) & 3, Y1 = (desc >> 8) & 3,
+        Y2 = (desc >> 10) & 3;
+    if (kind == 0) {
+        int nY = sh.es[sg][Y1 + 1] - sh.es[sg][Y1];
+        int i = loc / nY, a = loc - i * nY;
+        r1 = r2 = sg * n + sh.ol[sg][sh.os[sg][X1] + i];
+        a1 = a2 = sg * n + sh.el[sg][sh.es[sg][Y1] + a];
+    } else if (kind == 1) {
+        int k2 = sh.os[sg][X2 + 1] - sh.os[sg][X2];
+        int e1 = sh.es[sg][Y1 + 1] - sh.es[sg][Y1], e2 = sh.es[sg][Y2 + 1] - sh.es[sg][Y2];
+        int nEP = pairs_of(e1, e2, Y1 == Y2);
+        int op = loc / nEP, ep = loc - op * nEP;
+        int i, j, a, b;
+        if (X1 == X2) tri_decode(op, i, j);
+        else { i = op / k2; j = op - i * k2; }
+        if (Y1 == Y2) tri_decode(ep, a, b);
+        else { a = ep / e2; b = ep - a * e2; }
+        r1 = sg * n + sh.ol[sg][sh.os[sg][X1] + i];
+        r2 = sg * n + sh.ol[sg][sh.os[sg][X2] + j];
+        a1 = sg * n + sh.el[sg][sh.es[sg][Y1] + a];
+        a2 = sg * n + sh.el[sg][sh.es[sg][Y2] + b];
+    } else {
+        int nYa = sh.es[0][Y1 + 1] - sh.es[0][Y1];
+        int nYb = sh.es[1][Y2 + 1] - sh.es[1][Y2];
+        int nXb = sh.os[1][X2 + 1] - sh.os[1][X2];
+        int nbeta = nXb * nYb;
+        int sa = loc / nbeta, sb = loc - sa * nbeta;
+        int ia = sa / nYa, aa = sa - ia * nYa;
+        int ib = sb / nYb, ab = sb - ib * nYb;
+        r1 = sh.ol[0][sh.os[0][X1] + ia];
+        a1 = sh.el[0][sh.es[0][Y1] + aa];
+        r2 = n + sh.ol[1][sh.os[1][X2] + ib];
+        a2 = n + sh.el[1][sh.es[1][Y2] + ab];
+    }
+}
+
+__device__ __forceinline__ bool active_only(unsigned desc) {
+    int kind = desc & 3, X1 = (desc >> 4) & 3, X2 = (desc >> 6) & 3, Y1 = (desc >> 8) & 3, Y2 = (desc >> 10) & 3;
+    if (kind == 0) return X1 == 1 && Y1 == 1;
+    return X1 == 1 && X2 == 1 && Y1 == 1 && Y2 == 1;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// <d|H|d> and <d|H_D|d> (lane-parallel over occupied pairs); label >= 0 required for H_D
+template <int W>
+__device__ void diagonals(const SysDev& S, const WarpSh& sh, const unsigned long long (&d)[2][W], int lane,
+                          double& hnn, double& hdnn) {
+    const int na_ = sh.os[0][3], nb_ = sh.os[1][3], N = na_ + nb_;
+    double h = 0.0, hd = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        int p = k < na_ ? sh.ol[0][k] : sh.ol[1][k - na_];
+        h += __ldg(S.h1 + p * S.n + p);
+        int cls = p < S.nc ? 0 : (p < S.nc + S.na ? 1 : 2);
+        if (cls == 1) hd += __ldg(S.hc + p * S.n + p);
+        else if (cls == 2) hd += __ldg(S.eps + p);
+    }
+    // core holes
+    for (int sg = 0; sg < 2; sg++) {
+        for (int k = lane; k < S.nc - sh.os[sg][1]; k += 32) hd -= __ldg(S.eps + sh.el[sg][k]);
+    }
+    const int npair = N * (N - 1) / 2;
+    for (int q = lane; q < npair; q += 32) {
+        int j, i;
+        tri_decode(q, i, j);
+        int si = i >= na_, sj = j >= na_;
+        int p1 = si ? sh.ol[1][i - na_] : sh.ol[0][i];
+        int p2 = sj ? sh.ol[1][j - na_] : sh.ol[0][j];
+        double v = eri_g(S, p1, p1, p2, p2);
+        if (si == sj) v -= eri_g(S, p1, p2, p2, p1);
+        h += v;
+        bool a1 = p1 >= S.nc && p1 < S.nc + S.na, a2 = p2 >= S.nc && p2 < S.nc + S.na;
+        if (a1 && a2) hd += v;
+    }
+    hnn = warp_sum(h) + S.e_nuc;
+    hdnn = warp_sum(hd) + S.e_core;
+}
+
+// ============================================================================ the walk
+
+enum { MODE_STEP = 0, MODE_DEBUG = 1 };
+
+struct LocalOut {
+    double S, EL, num, hnn, hdnn;
+    int nnb;
+};
+
+// One local evaluation at det n (walker) with amplitude psin.  In MODE_STEP also picks the move;
+// in MODE_DEBUG writes neighbour records.  Returns the quantities on every lane.
+template <int W, int MODE, class C>
+__device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long long (&n)[2][W], double psin,
+                               long long ln, int h, int p, unsigned step, unsigned wid, int lane,
+                               unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc,
+                               mrq_neighbour* nbout, long long max_nb, C& ctr) {
+    build_lists<W>(S, n, sh, h, p, lane);
+    const int total = sh.bstart[sh.nb];
+    const double c0 = __ldg(S.c);
+    const double inv_psin = psin != 0.0 ? 1.0 / psin : 0.0;   // zero-amplitude determinants: ratios 0
+    double sS = 0.0, sH = 0.0, sHD = 0.0;
+    double bt = INFINITY;
+    float btf = INFINITY;
+    unsigned bexc = 0xFFFFFFFFu;
+    double bpsi = 0.0;
+    unsigned long long bm[2][W];
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+        for (int w = 0; w < W; w++) bm[sg][w] = n[sg][w];
+    int b = 0;
+    for (int idx = lane; idx < total; idx += 32) {
+        while (idx >= sh.bstart[b + 1]) b++;
+        const unsigned desc = sh.bdesc[b];
+        int kind, r1, r2, a1, a2;
+        decode_exc(sh, S.n, desc, idx - sh.bstart[b], kind, r1, r2, a1, a2);
+        unsigned long long m[2][W];
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
+        {
+            int s1 = r1 >= S.n, s2 = a1 >= S.n;
+            flip<W>(m[s1], r1 - s1 * S.n);
+            flip<W>(m[s2], a1 - s2 * S.n);
+            if (kind != 0) {
+                int s3 = r2 >= S.n, s4 = a2 >= S.n;
+                flip<W>(m[s3], r2 - s3 * S.n);
+                flip<W>(m[s4], a2 - s4 * S.n);
+            }
+        }
+        const double hnm =
+            (kind == 0) ? single_elem<W>(S, n, r1, a1, ctr) : double_elem<W>(S, n, r1, r2, a1, a2, ctr);
+        int hm, pm;
+        const long long lm = det_label<W>(S, m, hm, pm);
+        double om, psim;
+        if (lm == 0) {
+            ctr.cand();
+            om = hash_lookup(S, hash_key(S, active_bits<W>(S, m[0]), active_bits<W>(S, m[1])), ctr);
+            psim = c0 * om;
+        } else {
+            om = reach_back<W>(S, m, ctr);
+            ctr.g();
+            psim = __ldg(S.c + lm) * om;
+        }
+        const double ratio = psim * inv_psin;
+        const double g = fabs(hnm * ratio);
+        sS += g;
+        sH += hnm * ratio;
+        double hd = 0.0;
+        if (ln > 0 && active_only(desc)) {
+            hd = (kind == 0) ? hd_single_elem<W>(S, n, r1, a1, ctr) : hnm;
+            sHD += hd * ratio;
+        }
+        const unsigned exc = (unsigned)r1 | ((unsigned)r2 << 8) | ((unsigned)a1 << 16) | ((unsigned)a2 << 24);
+        if (MODE == MODE_STEP) {
+            if (g > 0.0) {
+                // exact FP64 clock only where a cheap FP32 bound says it can win
+                const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
+                const float tf = race_clock_f32(k53, (float)g);
+                if (!(tf > btf * 1.0001f)) {
+                    const double t = race_clock_f64(k53, g);
+                    if (t < bt || (t == bt && exc < bexc)) {
+                        btf = (float)t;
+                        bt = t;
+                        bexc = exc;
+                        bpsi = psim;
+#pragma unroll
+                        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+                            for (int w = 0; w < W; w++) bm[sg][w] = m[sg][w];
+                    }
+                }
+            }
+        } else {
+            if (nbout != nullptr && idx < max_nb) {
+                mrq_neighbour& r = nbout[idx];
+#pragma unroll
+                for (int w = 0; w < 4; w++) r.det[w] = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    r.det[w] = m[0][w];
+                    r.det[W + w] = m[1][w];
+                }
+                r.h = hnm;
+                r.hd = hd;
+                r.o = om;
+                r.psi = psim;
+                r.gamma = g;
+                r.exc = exc;
+                r.pad = 0;
+            }
+        }
+    }
+    LocalOut out;
+    out.S = warp_sum(sS);
+    const double eh = warp_sum(sH);
+    const double ehd = warp_sum(sHD);
+    double hnn, hdnn;
+    diagonals<W>(S, sh, n, lane, hnn, hdnn);
+    out.hnn = hnn;
+    out.hdnn = hdnn;
+    out.EL = hnn + eh;
+    out.num = ln > 0 ? hdnn + ehd : 0.0;
+    out.nnb = total;
+    if (MODE == MODE_STEP) {
+        // warp argmin over (clock, exc)
+        double t = bt;
+        unsigned e = bexc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double t2 = __shfl_xor_sync(0xffffffffu, t, o);
+            unsigned e2 = __shfl_xor_sync(0xffffffffu, e, o);
+            if (t2 < t || (t2 == t && e2 < e)) {
+                t = t2;
+                e = e2;
+            }
+        }
+        unsigned win = __ballot_sync(0xffffffffu, bexc == e && bt == t);
+        int src = win ? __ffs(win) - 1 : 0;
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) best[sg][w] = __shfl_sync(0xffffffffu, bm[sg][w], src);
+        best_psi = __shfl_sync(0xffffffffu, bpsi, src);
+        best_exc = e;
+    }
+    return out;
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) k_walk(const SysDev* __restrict__ systems, Walker* __restrict__ walkers,
+                                              long long nslots, int nsteps) {
+    __shared__ WarpSh shs[4];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const long long slot = (long long)blockIdx.x * 4 + wi;
+    if (slot >= nslots) return;
+    WarpSh& sh = shs[wi];
+    Walker wk = walkers[slot];
+    const SysDev S = systems[wk.sys];
+    unsigned long long n[2][W];
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+        for (int w = 0; w < W; w++) n[sg][w] = wk.d[sg][w];
+    double psin = wk.psi;
+    for (int s = 0; s < nsteps; s++) {
+        int h, p;
+        const long long ln = det_label<W>(S, n, h, p);
+        unsigned long long nxt[2][W];
+        double npsi = 0.0;
+        unsigned nexc = 0;
+        NoCtr nc;
+        LocalOut lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc,
+                                              nullptr, 0, nc);
+        if (!(lo.S > 0.0) || ln < 0) {
+            if (lane == 0) atomicOr(S.err, ln < 0 ? MRQ_ERR_LABEL : MRQ_ERR_NOMOVE);
+            break;
+        }
+        if (lane == 0 && (long long)wk.step >= S.burn_in) {
+            const double w = 1.0 / lo.S;
+            const double cl = __ldg(S.c + ln);
+            const double c2 = cl * cl;
+            const long long base = (long long)wk.group * S.nlab;
+            atomicAdd(S.accN + base + ln, w / c2);
+            if (ln > 0) atomicAdd(S.accU + base + ln, (w * lo.num) / c2);
+            atomicAdd(S.accW + wk.group, w);
+            atomicAdd(S.accE + wk.group, w * lo.EL);
+            atomicAdd(S.type_steps + 3 * h + p, 1ull);
+        }
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) n[sg][w] = nxt[sg][w];
+        psin = npsi;
+        wk.step++;
+        __syncwarp();
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) wk.d[sg][w] = n[sg][w];
+        wk.psi = psin;
+        walkers[slot] = wk;
+    }
+}
+
+// local quantities of arbitrary determinants (parity)
+template <int W>
+__global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, const unsigned long long* __restrict__ dets,
+                                               long long ndet, mrq_local* __restrict__ out, long long max_nb,
+                                               mrq_neighbour* __restrict__ nb) {
+    __shared__ WarpSh shs[4];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const long long i = (long long)blockIdx.x * 4 + wi;
+    if (i >= ndet) return;
+    WarpSh& sh = shs[wi];
+    const SysDev S = *sys;
+    unsigned long long n[2][W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        n[0][w] = dets[i * 2 * W + w];
+        n[1][w] = dets[i * 2 * W + W + w];
+    }
+    int h, p;
+    const long long ln = det_label<W>(S, n, h, p);
+    mrq_local r;
+    memset(&r, 0, sizeof r);
+    r.label = ln;
+    r.type = 3 * h + p;
+    if (ln < 0) {
+        if (lane == 0) out[i] = r;
+        return;
+    }
+    double psin;
+    NoCtr nc0;
+    if (ln == 0) psin = __ldg(S.c) * hash_lookup(S, hash_key(S, active_bits<W>(S, n[0]), active_bits<W>(S, n[1])), nc0);
+    else psin = __ldg(S.c + ln) * reach_back<W>(S, n, nc0);
+    psin = __shfl_sync(0xffffffffu, psin, 0);
+    unsigned long long dummy[2][W];
+    double dpsi;
+    unsigned dexc;
+    Ctr ctr;
+    LocalOut lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc,
+                                           nb ? nb + i * max_nb : nullptr, max_nb, ctr);
+    unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cg += __shfl_xor_sync(0xffffffffu, cg, o);
+        cp += __shfl_xor_sync(0xffffffffu, cp, o);
+        cc += __shfl_xor_sync(0xffffffffu, cc, o);
+    }
+    if (lane == 0) {
+        r.n_gathers = (long long)cg;
+        r.n_probes = (long long)cp;
+        r.n_candidates = (long long)cc;
+        r.S = lo.S;
+        r.e_local = lo.EL;
+        r.num = lo.num;
+        r.h_nn = lo.hnn;
+        r.hd_nn = lo.hdnn;
+        r.psi = psin;
+        r.n_neighbours = lo.nnb;
+        out[i] = r;
+    }
+}
+
+__global__ void k_walkers_init(Walker* w, long long nslots, unsigned long long d0, unsigned long long d1,
+                               unsigned long long d2, unsigned long long d3, double psi, int sys, int G) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nslots) return;
+    Walker x;
+    x.d[0][0] = d0; x.d[0][1] = d1; x.d[1][0] = d2; x.d[1][1] = d3;
+    x.psi = psi;
+    x.step = 0;
+    x.wid = (unsigned)i;
+    x.sys = sys;
+    x.group = (int)(i % G);
+    w[i] = x;
+}
+
+// ============================================================================ setup kernels
+
+// insert reference determinants (and validate them: full core, empty virtuals, electron counts)
+template <int W>
+__global__ void k_hash_build(const SysDev* __restrict__ sys, HashSlot* __restrict__ hash, const unsigned long long* dets,
+                             const double* coeffs, long long nref, int* err) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nref) return;
+    const SysDev S = *sys;
+    unsigned long long d[2][W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        d[0][w] = dets[i * 2 * W + w];
+        d[1][w] = dets[i * 2 * W + W + w];
+    }
+    int ca = 0, cb = 0;
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        ca += __popcll(d[0][w]);
+        cb += __popcll(d[1][w]);
+        unsigned long long all = S.mcore[w] | S.mact[w] | S.mvirt[w];
+        for (int sg = 0; sg < 2; sg++) {
+            if ((d[sg][w] & S.mcore[w]) != S.mcore[w]) bad = true;
+            if (d[sg][w] & S.mvirt[w]) bad = true;
+            if (d[sg][w] & ~all) bad = true;
+        }
+    }
+    if (ca != S.nalpha || cb != S.nbeta) bad = true;
+    if (bad) {
+        atomicOr(err, 8);
+        return;
+    }
+    unsigned long long key = hash_key(S, active_bits<W>(S, d[0]), active_bits<W>(S, d[1]));
+    unsigned long long hidx = mix64(key) & S.hmask;
+    for (int k = 0; k < S.max_probe; k++) {
+        unsigned long long prev = atomicCAS(&hash[hidx].key, MRQ_EMPTY_KEY, key);
+        if (prev == MRQ_EMPTY_KEY) {
+            hash[hidx].val = coeffs[i];
+            return;
+        }
+        if (prev == key) {
+            atomicOr(err, 16);   // duplicate determinant
+            return;
+        }
+        hidx = (hidx + 1) & S.hmask;
+    }
+    atomicOr(err, 32);   // probe bound exceeded
+}
+
+__global__ void k_hash_clear(HashSlot* hash, unsigned long long cap) {
+    unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cap) {
+        hash[i].key = MRQ_EMPTY_KEY;
+        hash[i].val = 0.0;
+    }
+}
+
+// hc_pq = h_pq + sum_i [2(pq|ii) - (pi|iq)]
+__global__ void k_core_fock(const SysDev* __restrict__ sys, double* hc) {
+    const SysDev S = *sys;
+    int pq = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pq >= S.n * S.n) return;
+    int p = pq / S.n, q = pq % S.n;
+    double v = __ldg(S.h1 + pq);
+    for (int i = 0; i < S.nc; i++) v += 2.0 * eri_g(S, p, q, i, i) - eri_g(S, p, i, i, q);
+    hc[pq] = v;
+}
+
+// block-level deterministic sum of `nv` values per thread into out[blockIdx.x * nv + k]
+template <int NV>
+__device__ void block_sum_store(double (&v)[NV], double* out) {
+    __shared__ double red[32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double x = warp_sum(v[k]);
+        if (lane == 0) red[wid][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += red[w][threadIdx.x];
+        out[(long long)blockIdx.x * NV + threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// E0 numerator and norm: sum_k c_k^2 H_kk + sum_k sum_{k' active exc} c_k H_kk' c_k'
+// one thread per (reference determinant, excitation) pair, strided; partials per block.
+template <int W>
+__global__ void k_ref_energy(const SysDev* __restrict__ sys, const unsigned long long* dets, const double* coeffs,
+                             long long nref, double* partial) {
+    const SysDev S = *sys;
+    double acc[2] = {0.0, 0.0};
+    const int na = S.na;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gsz = (long long)gridDim.x * blockDim.x;
+    for (long long i = gtid; i < nref; i += gsz) {
+        unsigned long long d[2][W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            d[0][w] = dets[i * 2 * W + w];
+            d[1][w] = dets[i * 2 * W + W + w];
+        }
+        const double ck = coeffs[i];
+        acc[1] += ck * ck;
+        // diagonal
+        double hdiag = S.e_nuc;
+        for (int sg = 0; sg < 2; sg++)
+            for (int w = 0; w < W; w++) {
+                unsigned long long om = d[sg][w];
+                while (om) {
+                    int p1 = 64 * w + __ffsll(om) - 1;
+                    om &= om - 1;
+                    hdiag += __ldg(S.h1 + p1 * S.n + p1);
+                    for (int sg2 = 0; sg2 < 2; sg2++)
+                        for (int w2 = 0; w2 < W; w2++) {
+                            unsigned long long om2 = d[sg2][w2];
+                            while (om2) {
+                                int p2 = 64 * w2 + __ffsll(om2) - 1;
+                                om2 &= om2 - 1;
+                                hdiag += 0.5 * eri_g(S, p1, p1, p2, p2);
+                                if (sg == sg2) hdiag -= 0.5 * eri_g(S, p1, p2, p2, p1);
+                            }
+                        }
+                }
+            }
+        double off = 0.0;
+        const unsigned ao[2] = {active_bits<W>(S, d[0]), active_bits<W>(S, d[1])};
+        const unsigned am = (na >= 32) ? 0xFFFFFFFFu : ((1u << na) - 1u);
+        // singles and same-spin doubles
+        for (int sg = 0; sg < 2; sg++) {
+            unsigned o1 = ao[sg];
+            while (o1) {
+                int t = __ffs(o1) - 1;
+                o1 &= o1 - 1;
+                unsigned e1 = ~ao[sg] & am;
+                while (e1) {
+                    int u = __ffs(e1) - 1;
+                    e1 &= e1 - 1;
+                    unsigned k0 = ao[0], k1 = ao[1];
+                    (sg ? k1 : k0) ^= (1u << t) | (1u << u);
+                    double c = hash_lookup(S, hash_key(S, k0, k1));
+                    NoCtr z;
+                    if (c != 0.0) off += ck * c * single_elem<W>(S, d, sg * S.n + S.nc + t, sg * S.n + S.nc + u, z);
+                }
+                unsigned o2 = o1;   // t2 > t
+                while (o2) {
+                    int t2 = __ffs(o2) - 1;
+                    o2 &= o2 - 1;
+                    unsigned e2 = ~ao[sg] & am;
+                    while (e2) {
+                        int u1 = __ffs(e2) - 1;
+                        e2 &= e2 - 1;
+                        unsigned e3 = e2;
+                        while (e3) {
+                            int u2 = __ffs(e3) - 1;
+                            e3 &= e3 - 1;
+                            unsigned k0 = ao[0], k1 = ao[1];
+                            (sg ? k1 : k0) ^= (1u << t) | (1u << t2) | (1u << u1) | (1u << u2);
+                            double c = hash_lookup(S, hash_key(S, k0, k1));
+                            if (c != 0.0) {
+                                int b = sg * S.n + S.nc;
+                                NoCtr z;
+                                off += ck * c * double_elem<W>(S, d, b + t, b + t2, b + u1, b + u2, z);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // opposite-spin doubles
+        {
+            unsigned oa = ao[0];
+            while (oa) {
+                int t = __ffs(oa) - 1;
+                oa &= oa - 1;
+                unsigned ea = ~ao[0] & am;
+                while (ea) {
+                    int u = __ffs(ea) - 1;
+                    ea &= ea - 1;
+                    unsigned ob = ao[1];
+                    while (ob) {
+                        int s = __ffs(ob) - 1;
+                        ob &= ob - 1;
+                        unsigned eb = ~ao[1] & am;
+                        while (eb) {
+                            int v = __ffs(eb) - 1;
+                            eb &= eb - 1;
+                            unsigned k0 = ao[0] ^ ((1u << t) | (1u << u));
+                            unsigned k1 = ao[1] ^ ((1u << s) | (1u << v));
+                            double c = hash_lookup(S, hash_key(S, k0, k1));
+                            NoCtr z;
+                            if (c != 0.0)
+                                off += ck * c *
+                                       double_elem<W>(S, d, S.nc + t, S.n + S.nc + s, S.nc + u, S.n + S.nc + v, z);
+                        }
+                    }
+                }
+            }
+        }
+        acc[0] += ck * ck * hdiag + off;
+    }
+    block_sum_store<2>(acc, partial);
+}
+
+// spin-summed active 1-RDM element gamma_tu (unnormalised): block (t, u) over all determinants
+template <int W>
+__global__ void k_ref_rdm(const SysDev* __restrict__ sys, const unsigned long long* dets, const double* coeffs,
+                          long long nref, double* gamma_raw) {
+    const SysDev S = *sys;
+    const int t = blockIdx.x / S.na, u = blockIdx.x % S.na;
+    double acc[1] = {0.0};
+    for (long long i = threadIdx.x; i < nref; i += blockDim.x) {
+        unsigned long long d[2][W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            d[0][w] = dets[i * 2 * W + w];
+            d[1][w] = dets[i * 2 * W + W + w];
+        }
+        const double ck = coeffs[i];
+        const unsigned ao[2] = {active_bits<W>(S, d[0]), active_bits<W>(S, d[1])};
+        for (int sg = 0; sg < 2; sg++) {
+            // <phi0| a+_t a_u |phi0>: d has u occupied; k' = d - u + t
+            if (!((ao[sg] >> u) & 1u)) continue;
+            if (t == u) {
+                acc[0] += ck * ck;
+                continue;
+            }
+            if ((ao[sg] >> t) & 1u) continue;
+            unsigned k0 = ao[0], k1 = ao[1];
+            (sg ? k1 : k0) ^= (1u << t) | (1u << u);
+            double c = hash_lookup(S, hash_key(S, k0, k1));
+            if (c != 0.0) acc[0] += ck * c * sgn_single<W>(d[sg], S.nc + u, S.nc + t);
+        }
+    }
+    // single block per (t,u): reduce and store
+    __shared__ double red[32];
+    double x = warp_sum(acc[0]);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) s += red[w];
+        gamma_raw[blockIdx.x] = s;
+    }
+}
+
+// reduce E0 partials (fixed order), normalise gamma, eps_p = F_pp, E_core; writes scal[0..4]
+__global__ void k_setup_finish(const SysDev* __restrict__ sys, const double* partial, int npart, double* gamma,
+                               double* eps, double* scal) {
+    const SysDev S = *sys;
+    __shared__ double s_num, s_norm;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < npart; i++) {
+            a += partial[2 * i];
+            b += partial[2 * i + 1];
+        }
+        s_num = a;
+        s_norm = b;
+    }
+    __syncthreads();
+    const int na = S.na;
+    for (int k = threadIdx.x; k < na * na; k += blockDim.x) gamma[k] /= s_norm;
+    __syncthreads();
+    for (int p = threadIdx.x; p < S.n; p += blockDim.x) {
+        double v = __ldg(S.hc + p * S.n + p);
+        for (int t = 0; t < na; t++)
+            for (int u = 0; u < na; u++)
+                v += gamma[t * na + u] * (eri_g(S, p, p, S.nc + t, S.nc + u) - 0.5 * eri_g(S, p, S.nc + t, S.nc + u, p));
+        eps[p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ec = S.e_nuc, se = 0.0;
+        for (int i = 0; i < S.nc; i++) {
+            ec += 2.0 * __ldg(S.h1 + i * S.n + i);
+            for (int j = 0; j < S.nc; j++) ec += 2.0 * eri_g(S, i, i, j, j) - eri_g(S, i, j, j, i);
+            se += eps[i];
+        }
+        scal[0] = s_num / s_norm;
+        scal[1] = s_norm;
+        scal[2] = ec;
+        scal[3] = se;
+    }
+}
+
+// index of the largest |c| (first on ties), one block
+__global__ void k_argmax_abs(const double* c, long long n, long long* out) {
+    __shared__ double bv[1024];
+    __shared__ long long bi[1024];
+    double v = -1.0;
+    long long idx = 0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        double a = fabs(c[i]);
+        if (a > v) { v = a; idx = i; }
+    }
+    bv[threadIdx.x] = v;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double v2 = bv[threadIdx.x + s];
+            long long i2 = bi[threadIdx.x + s];
+            if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+                bv[threadIdx.x] = v2;
+                bi[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = bi[0];
+}
+
+// ============================================================================ finalize (Eq. 14-15)
+
+#define FIN_Q 5    // per type: kept ratio, e2, screened count, screened ratio, visited count
+#define FIN_NV (MRQ_NTYPES * FIN_Q)
+
+__device__ __forceinline__ int label_type(long long l, long long nPs, int nc2, int nv2) {
+    long long rh = l / nPs, rp = l - rh * nPs;
+    int h = rh == 0 ? 0 : (rh <= nc2 ? 1 : 2);
+    int p = rp == 0 ? 0 : (rp <= nv2 ? 1 : 2);
+    return 3 * h + p;
+}
+
+// block (v, chunk): labels of the chunk under variant v (v < G: group v left out; v == G: all)
+__global__ void __launch_bounds__(256) k_fin_labels(const SysDev* __restrict__ sys, double tau, int nchunk,
+                                                    long long chunk, double* partial) {
+    const SysDev S = *sys;
+    const int v = blockIdx.x / nchunk, ch = blockIdx.x % nchunk;
+    const int G = S.G;
+    const long long L = S.nlab;
+    __shared__ double s_n0;
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int g = 0; g < G; g++) a += S.accN[(long long)g * L];
+        if (v < G) a -= S.accN[(long long)v * L];
+        s_n0 = a;
+    }
+    __syncthreads();
+    const double n0 = s_n0;
+    double acc[FIN_NV];
+#pragma unroll
+    for (int k = 0; k < FIN_NV; k++) acc[k] = 0.0;
+    const long long lo = (long long)ch * chunk, hi = min(L, lo + chunk);
+    for (long long l = lo + threadIdx.x; l < hi; l += blockDim.x) {
+        if (l == 0) continue;
+        double Nl = 0.0, Ul = 0.0;
+        for (int g = 0; g < G; g++) {
+            Nl += S.accN[(long long)g * L + l];
+            Ul += S.accU[(long long)g * L + l];
+        }
+        if (v < G) {
+            Nl -= S.accN[(long long)v * L + l];
+            Ul -= S.accU[(long long)v * L + l];
+        }
+        if (!(Nl > 0.0)) continue;
+        const int t = label_type(l, S.nPs, 2 * S.nc, 2 * S.nv);
+        const double ratio = Nl / n0;
+        double q[FIN_Q] = {0.0, 0.0, 0.0, 0.0, 1.0};
+        if (ratio >= tau) {
+            const double El = Ul / Nl;
+            q[0] = ratio;
+            q[1] = ratio / (S.e0 - El);
+        } else {
+            q[2] = 1.0;
+            q[3] = ratio;
+        }
+#pragma unroll
+        for (int tt = 0; tt < MRQ_NTYPES; tt++)
+            if (tt == t) {
+#pragma unroll
+                for (int k = 0; k < FIN_Q; k++) acc[tt * FIN_Q + k] += q[k];
+            }
+    }
+    block_sum_store<FIN_NV>(acc, partial);
+}
+
+// one block: sum chunk partials in order, jackknife over groups, write the result struct
+__global__ void k_fin_reduce(const SysDev* __restrict__ sys, const double* partial, int nchunk, mrq_result* res) {
+    const SysDev S = *sys;
+    const int G = S.G;
+    const long long L = S.nlab;
+    __shared__ double vals[65][FIN_NV];   // G <= 64
+    for (int idx = threadIdx.x; idx < (G + 1) * FIN_NV; idx += blockDim.x) {
+        int v = idx / FIN_NV, k = idx % FIN_NV;
+        double s = 0.0;
+        for (int c = 0; c < nchunk; c++) s += partial[((long long)v * nchunk + c) * FIN_NV + k];
+        vals[v][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double Wt = 0.0, Et = 0.0, N0t = 0.0;
+    for (int g = 0; g < G; g++) {
+        Wt += S.accW[g];
+        Et += S.accE[g];
+        N0t += S.accN[(long long)g * L];
+    }
+    const double c0 = S.c[0];
+    auto scal = [&](int v, double& e2, double& ev, double& a0) {
+        double Wv = Wt - (v < G ? S.accW[v] : 0.0);
+        double Ev = Et - (v < G ? S.accE[v] : 0.0);
+        double N0v = N0t - (v < G ? S.accN[(long long)v * L] : 0.0);
+        e2 = 0.0;
+        for (int t = 0; t < MRQ_NTYPES; t++) e2 += vals[v][t * FIN_Q + 1];
+        ev = Ev / Wv;
+        a0 = c0 * c0 * N0v / Wv;
+    };
+    double e2f, evf, a0f;
+    scal(G, e2f, evf, a0f);
+    res->e0 = S.e0;
+    res->e2 = e2f;
+    res->e_var = evf;
+    res->a0sq = a0f;
+    res->e_mrci_q = evf + (1.0 - a0f) * (evf - S.e0);
+    // jackknife
+    double m_e2 = 0, m_ev = 0, m_a0 = 0, tn_m[MRQ_NTYPES], te_m[MRQ_NTYPES];
+    for (int t = 0; t < MRQ_NTYPES; t++) tn_m[t] = te_m[t] = 0.0;
+    for (int g = 0; g < G; g++) {
+        double a, b, c;
+        scal(g, a, b, c);
+        m_e2 += a; m_ev += b; m_a0 += c;
+        for (int t = 0; t < MRQ_NTYPES; t++) {
+            tn_m[t] += vals[g][t * FIN_Q + 0];
+            te_m[t] += vals[g][t * FIN_Q + 1];
+        }
+    }
+    m_e2 /= G; m_ev /= G; m_a0 /= G;
+    for (int t = 0; t < MRQ_NTYPES; t++) { tn_m[t] /= G; te_m[t] /= G; }
+    double v_e2 = 0, v_ev = 0, v_a0 = 0, tn_v[MRQ_NTYPES], te_v[MRQ_NTYPES];
+    for (int t = 0; t < MRQ_NTYPES; t++) tn_v[t] = te_v[t] = 0.0;
+    for (int g = 0; g < G; g++) {
+        double a, b, c;
+        scal(g, a, b, c);
+        v_e2 += (a - m_e2) * (a - m_e2);
+        v_ev += (b - m_ev) * (b - m_ev);
+        v_a0 += (c - m_a0) * (c - m_a0);
+        for (int t = 0; t < MRQ_NTYPES; t++) {
+            double x = vals[g][t * FIN_Q + 0] - tn_m[t], y = vals[g][t * FIN_Q + 1] - te_m[t];
+            tn_v[t] += x * x;
+            te_v[t] += y * y;
+        }
+    }
+    const double f = G > 1 ? (double)(G - 1) / G : NAN;
+    res->e2_sigma = sqrt(f * v_e2);
+    res->e_var_sigma = sqrt(f * v_ev);
+    res->a0sq_sigma = sqrt(f * v_a0);
+    double scr_norm = 0.0, visited = 0.0;
+    long long wsteps = 0;
+    for (int t = 0; t < MRQ_NTYPES; t++) {
+        res->type_norm[t] = vals[G][t * FIN_Q + 0];
+        res->type_e2[t] = vals[G][t * FIN_Q + 1];
+        res->type_screened[t] = vals[G][t * FIN_Q + 2];
+        res->type_norm_sigma[t] = sqrt(f * tn_v[t]);
+        res->type_e2_sigma[t] = sqrt(f * te_v[t]);
+        scr_norm += vals[G][t * FIN_Q + 3];
+        visited += vals[G][t * FIN_Q + 4];
+        res->type_steps[t] = (long long)S.type_steps[t];
+        wsteps += (long long)S.type_steps[t];
+    }
+    res->screened_norm = scr_norm;
+    res->n_labels_visited = visited;
+    res->walker_steps = wsteps;
+}
+
+// ============================================================================ host runtime
+
+struct mrq_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char err[1024] = {0};
+    // Hamiltonian
+    bool ham = false;
+    int n = 0, nc = 0, na = 0, nv = 0, W = 1, nalpha = 0, nbeta = 0;
+    double e_nuc = 0.0;
+    long long neri = 0;
+    double *d_h1 = nullptr, *d_eri = nullptr, *d_hc = nullptr, *d_eps = nullptr, *d_gamma = nullptr;
+    long long nHs = 0, nPs = 0, nlab = 0;
+    // reference
+    bool ref = false;
+    long long nref = 0;
+    HashSlot* d_hash = nullptr;
+    unsigned long long hcap = 0;
+    unsigned long long start[4] = {0, 0, 0, 0};
+    double start_c = 0.0;
+    long long start_idx = 0;
+    double e0 = 0, norm0 = 0, e_core = 0, sum_eps_core = 0;
+    std::vector<double> eps, gamma;
+    // coefficients
+    double* d_c = nullptr;
+    // walkers / accumulators
+    Walker* d_walk = nullptr;
+    long long nwalk = 0, walk_cap = 0;
+    int G = 0;
+    long long burn = 0;
+    unsigned long long seed = 0;
+    double tau = 1e-10;
+    double *d_accN = nullptr, *d_accU = nullptr, *d_accW = nullptr, *d_accE = nullptr;
+    unsigned long long* d_types = nullptr;
+    long long acc_lab = 0;
+    int acc_G = 0;
+    int* d_err = nullptr;
+    double* d_partial = nullptr;
+    long long partial_cap = 0;
+    mrq_result* d_res = nullptr;
+    SysDev hsys{};
+    SysDev* d_sys = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> evs;    // start/stop pairs of the walk launches since the last finalize
+    int launches = 0;
+    long long launches_total = 0;
+    double walk_ms = 0.0;
+    long long total_steps = 0;
+};
+
+static int fail(mrq_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MRQ_OOM : MRQ_CUDA_ERROR, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+    } while (0)
+
+template <typename T>
+static void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+static void free_reference(mrq_ctx* c) {
+    dfree(c->d_hash);
+    dfree(c->d_c);
+    c->ref = false;
+}
+static void free_walkers(mrq_ctx* c) {
+    dfree(c->d_walk);
+    dfree(c->d_accN);
+    dfree(c->d_accU);
+    dfree(c->d_accW);
+    dfree(c->d_accE);
+    dfree(c->d_types);
+    dfree(c->d_partial);
+    c->nwalk = c->walk_cap = 0;
+    c->acc_lab = 0;
+    c->acc_G = 0;
+    c->partial_cap = 0;
+}
+static void free_hamiltonian(mrq_ctx* c) {
+    dfree(c->d_h1);
+    dfree(c->d_eri);
+    dfree(c->d_hc);
+    dfree(c->d_eps);
+    dfree(c->d_gamma);
+    c->ham = false;
+}
+
+static int push_sys(mrq_ctx* ctx) {
+    SysDev& s = ctx->hsys;
+    s.accN = ctx->d_accN;
+    s.accU = ctx->d_accU;
+    s.accW = ctx->d_accW;
+    s.accE = ctx->d_accE;
+    s.type_steps = ctx->d_types;
+    s.G = ctx->G;
+    s.burn_in = ctx->burn;
+    s.seed = ctx->seed;
+    s.err = ctx->d_err;
+    s.c = ctx->d_c;
+    s.hash = ctx->d_hash;
+    s.hmask = ctx->hcap ? ctx->hcap - 1 : 0;
+    s.e0 = ctx->e0;
+    s.e_core = ctx->e_core;
+    s.sum_eps_core = ctx->sum_eps_core;
+    CK(cudaMemcpyAsync(ctx->d_sys, &s, sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
+    return 0;
+}
+
+static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *flag_out = f;
+    return 0;
+}
+
+extern "C" {
+
+int mrq_create(mrq_ctx** out, int device) {
+    if (!out) return MRQ_INVALID_ARG;
+    *out = nullptr;
+    mrq_ctx* ctx = new mrq_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return MRQ_CUDA_ERROR;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMalloc(&ctx->d_sys, sizeof(SysDev)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_res, sizeof(mrq_result)) != cudaSuccess || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        mrq_destroy(ctx);
+        return MRQ_CUDA_ERROR;
+    }
+    ctx->own_stream = true;
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    *out = ctx;
+    return 0;
+}
+
+void mrq_destroy(mrq_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_walkers(ctx);
+    free_reference(ctx);
+    free_hamiltonian(ctx);
+    dfree(ctx->d_err);
+    dfree(ctx->d_sys);
+    dfree(ctx->d_res);
+    for (auto e : ctx->evs) cudaEventDestroy(e);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* mrq_last_error(const mrq_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+int mrq_set_stream(mrq_ctx* ctx, void* stream) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (stream) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        ctx->stream = (cudaStream_t)stream;
+        ctx->own_stream = false;
+    } else if (!ctx->own_stream) {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    return 0;
+}
+
+int64_t mrq_n_labels(const mrq_ctx* ctx) { return (ctx && ctx->ham) ? ctx->nlab : 0; }
+
+int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_alpha, int n_beta, const double* h1,
+                         const double* eri, double e_core) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    const int n = n_core + n_act + n_virt;
+    if (n_core < 0 || n_act < 0 || n_virt < 0 || n <= 0 || n > MRQ_MAXN || n_core > 64 || n_act > 32 || !h1 ||
+        !eri)
+        return fail(ctx, MRQ_INVALID_ARG, "orbital counts out of range (n <= 128, n_core <= 64, n_act <= 32)");
+    if (n_alpha < n_core || n_beta < n_core || n_alpha > n_core + n_act || n_beta > n_core + n_act)
+        return fail(ctx, MRQ_INVALID_ARG, "electron counts must fill the core and fit the active space");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_walkers(ctx);
+    free_reference(ctx);
+    free_hamiltonian(ctx);
+    ctx->n = n;
+    ctx->nc = n_core;
+    ctx->na = n_act;
+    ctx->nv = n_virt;
+    ctx->W = (n + 63) / 64;
+    ctx->nalpha = n_alpha;
+    ctx->nbeta = n_beta;
+    ctx->e_nuc = e_core;
+    const long long npair = (long long)n * (n + 1) / 2;
+    ctx->neri = npair * (npair + 1) / 2;
+    ctx->nHs = 1 + 2LL * n_core + (2LL * n_core) * (2LL * n_core - 1) / 2;
+    ctx->nPs = 1 + 2LL * n_virt + (2LL * n_virt) * (2LL * n_virt - 1) / 2;
+    ctx->nlab = ctx->nHs * ctx->nPs;
+    CK(cudaMalloc(&ctx->d_h1, sizeof(double) * n * n));
+    CK(cudaMalloc(&ctx->d_eri, sizeof(double) * ctx->neri));
+    CK(cudaMalloc(&ctx->d_hc, sizeof(double) * n * n));
+    CK(cudaMalloc(&ctx->d_eps, sizeof(double) * n));
+    CK(cudaMalloc(&ctx->d_gamma, sizeof(double) * std::max(1, n_act * n_act)));
+    CK(cudaMemcpyAsync(ctx->d_h1, h1, sizeof(double) * n * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_eri, eri, sizeof(double) * ctx->neri, cudaMemcpyDefault, ctx->stream));
+    SysDev& s = ctx->hsys;
+    s = SysDev{};
+    s.n = n;
+    s.nc = n_core;
+    s.na = n_act;
+    s.nv = n_virt;
+    s.W = ctx->W;
+    s.nalpha = n_alpha;
+    s.nbeta = n_beta;
+    s.nPs = ctx->nPs;
+    s.nlab = ctx->nlab;
+    for (int w = 0; w < 2; w++) {
+        s.mcore[w] = s.mact[w] = s.mvirt[w] = 0;
+        for (int q = 64 * w; q < 64 * w + 64 && q < n; q++) {
+            unsigned long long b = 1ull << (q - 64 * w);
+            if (q < n_core) s.mcore[w] |= b;
+            else if (q < n_core + n_act) s.mact[w] |= b;
+            else s.mvirt[w] |= b;
+        }
+    }
+    s.eri = ctx->d_eri;
+    s.h1 = ctx->d_h1;
+    s.hc = ctx->d_hc;
+    s.eps = ctx->d_eps;
+    s.e_nuc = e_core;
+    s.max_probe = 64;
+    s.G = 1;
+    if (int r = push_sys(ctx)) return r;
+    k_core_fock<<<(n * n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hc);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ham = true;
+    return 0;
+}
+
+int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const double* coeffs) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ham) return fail(ctx, MRQ_NOT_LOADED, "load the Hamiltonian first");
+    if (n_det <= 0 || !dets || !coeffs) return fail(ctx, MRQ_INVALID_ARG, "empty reference");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_walkers(ctx);
+    free_reference(ctx);
+    const int W = ctx->W;
+    unsigned long long cap = 16;
+    while (cap < 2ull * (unsigned long long)n_det) cap <<= 1;
+    ctx->hcap = cap;
+    ctx->nref = n_det;
+    unsigned long long* d_dets = nullptr;
+    double* d_co = nullptr;
+    CK(cudaMalloc(&ctx->d_hash, sizeof(HashSlot) * cap));
+    CK(cudaMalloc(&d_dets, sizeof(unsigned long long) * 2 * W * n_det));
+    CK(cudaMalloc(&d_co, sizeof(double) * n_det));
+    CK(cudaMalloc(&ctx->d_c, sizeof(double) * ctx->nlab));
+    CK(cudaMemcpyAsync(d_dets, dets, sizeof(unsigned long long) * 2 * W * n_det, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(d_co, coeffs, sizeof(double) * n_det, cudaMemcpyDefault, ctx->stream));
+    {
+        std::vector<double> c(ctx->nlab, 0.1);
+        c[0] = 1.0;
+        CK(cudaMemcpyAsync(ctx->d_c, c.data(), sizeof(double) * ctx->nlab, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    if (int r = push_sys(ctx)) return r;
+    k_hash_clear<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_hash, cap);
+    const unsigned nbk = (unsigned)((n_det + 127) / 128);
+    if (W == 1) k_hash_build<1><<<nbk, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hash, d_dets, d_co, n_det, ctx->d_err);
+    else k_hash_build<2><<<nbk, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hash, d_dets, d_co, n_det, ctx->d_err);
+    CK(cudaGetLastError());
+    int flag = 0;
+    if (int r = check_err_flag(ctx, &flag)) return r;
+    if (flag) {
+        cudaFree(d_dets);
+        cudaFree(d_co);
+        free_reference(ctx);
+        if (flag & 32) return fail(ctx, MRQ_HASH_OVERFLOW, "hash insertion ran past the probe bound");
+        return fail(ctx, MRQ_BAD_REFERENCE, "reference determinant with a core hole, a virtual electron, "
+                                            "a wrong electron count or a duplicate (flags %d)", flag);
+    }
+    // start determinant: largest |c| (first on ties)
+    long long* d_idx = nullptr;
+    CK(cudaMalloc(&d_idx, sizeof(long long)));
+    k_argmax_abs<<<1, 1024, 0, ctx->stream>>>(d_co, n_det, d_idx);
+    CK(cudaMemcpyAsync(&ctx->start_idx, d_idx, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_idx);
+    memset(ctx->start, 0, sizeof ctx->start);
+    {
+        unsigned long long tmp[4] = {0, 0, 0, 0};
+        CK(cudaMemcpy(tmp, d_dets + ctx->start_idx * 2 * W, sizeof(unsigned long long) * 2 * W, cudaMemcpyDeviceToHost));
+        for (int w = 0; w < W; w++) {
+            ctx->start[w] = tmp[w];
+            ctx->start[2 + w] = tmp[W + w];
+        }
+        CK(cudaMemcpy(&ctx->start_c, d_co + ctx->start_idx, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    // E0, norm, gamma, eps
+    const int nblk = 304;
+    double* d_part = nullptr;
+    double* d_scal = nullptr;
+    CK(cudaMalloc(&d_part, sizeof(double) * 2 * nblk));
+    CK(cudaMalloc(&d_scal, sizeof(double) * 8));
+    if (W == 1) k_ref_energy<1><<<nblk, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, d_co, n_det, d_part);
+    else k_ref_energy<2><<<nblk, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, d_co, n_det, d_part);
+    CK(cudaGetLastError());
+    if (ctx->na > 0) {
+        if (W == 1) k_ref_rdm<1><<<ctx->na * ctx->na, 256, 0, ctx->stream>>>(ctx->d_sys, d_dets, d_co, n_det, ctx->d_gamma);
+        else k_ref_rdm<2><<<ctx->na * ctx->na, 256, 0, ctx->stream>>>(ctx->d_sys, d_dets, d_co, n_det, ctx->d_gamma);
+        CK(cudaGetLastError());
+    }
+    k_setup_finish<<<1, 256, 0, ctx->stream>>>(ctx->d_sys, d_part, nblk, ctx->d_gamma, ctx->d_eps, d_scal);
+    CK(cudaGetLastError());
+    double scal[8];
+    CK(cudaMemcpyAsync(scal, d_scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->eps.assign(ctx->n, 0.0);
+    ctx->gamma.assign((size_t)ctx->na * ctx->na, 0.0);
+    CK(cudaMemcpyAsync(ctx->eps.data(), ctx->d_eps, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->na)
+        CK(cudaMemcpyAsync(ctx->gamma.data(), ctx->d_gamma, sizeof(double) * ctx->na * ctx->na, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_part);
+    cudaFree(d_scal);
+    cudaFree(d_dets);
+    cudaFree(d_co);
+    ctx->e0 = scal[0];
+    ctx->norm0 = scal[1];
+    ctx->e_core = scal[2];
+    ctx->sum_eps_core = scal[3];
+    int flag2 = 0;
+    if (int r = check_err_flag(ctx, &flag2)) return r;
+    if (flag2 & MRQ_ERR_HASH) return fail(ctx, MRQ_HASH_OVERFLOW, "hash probe bound exceeded during setup");
+    if (int r = push_sys(ctx)) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ref = true;
+    return 0;
+}
+
+int mrq_set_coeffs(mrq_ctx* ctx, int64_t n_labels, const double* c) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "load the Hamiltonian and the reference first");
+    if (n_labels != ctx->nlab || !c)
+        return fail(ctx, MRQ_INVALID_ARG, "expected %lld coefficients", (long long)ctx->nlab);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(ctx->d_c, c, sizeof(double) * n_labels, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+int mrq_setup_info(mrq_ctx* ctx, double* out5, double* eps, double* gamma) {
+    if (!ctx || !out5) return MRQ_INVALID_ARG;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
+    out5[0] = ctx->e0;
+    out5[1] = ctx->norm0;
+    out5[2] = ctx->e_core;
+    out5[3] = ctx->sum_eps_core;
+    out5[4] = (double)ctx->start_idx;
+    if (eps) memcpy(eps, ctx->eps.data(), sizeof(double) * ctx->n);
+    if (gamma && ctx->na) memcpy(gamma, ctx->gamma.data(), sizeof(double) * ctx->na * ctx->na);
+    return 0;
+}
+
+int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* local, int64_t max_nb,
+                    mrq_neighbour* nb) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
+    if (n <= 0 || !dets || !local || (nb && max_nb <= 0)) return fail(ctx, MRQ_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    const int W = ctx->W;
+    unsigned long long* d_dets = nullptr;
+    mrq_local* d_loc = nullptr;
+    mrq_neighbour* d_nb = nullptr;
+    CK(cudaMalloc(&d_dets, sizeof(unsigned long long) * 2 * W * n));
+    CK(cudaMalloc(&d_loc, sizeof(mrq_local) * n));
+    if (nb) CK(cudaMalloc(&d_nb, sizeof(mrq_neighbour) * n * max_nb));
+    CK(cudaMemcpyAsync(d_dets, dets, sizeof(unsigned long long) * 2 * W * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    if (int r = push_sys(ctx)) return r;
+    const unsigned blocks = (unsigned)((n + 3) / 4);
+    if (W == 1) k_debug<1><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb);
+    else k_debug<2><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(local, d_loc, sizeof(mrq_local) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nb) CK(cudaMemcpyAsync(nb, d_nb, sizeof(mrq_neighbour) * n * max_nb, cudaMemcpyDeviceToHost, ctx->stream));
+    int flag = 0;
+    if (int r = check_err_flag(ctx, &flag)) return r;
+    cudaFree(d_dets);
+    cudaFree(d_loc);
+    if (d_nb) cudaFree(d_nb);
+    if (flag & MRQ_ERR_HASH) return fail(ctx, MRQ_HASH_OVERFLOW, "hash probe bound exceeded");
+    return 0;
+}
+
+int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
+    if (!ctx || !p) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
+    if (p->n_walkers <= 0 || p->n_groups <= 0 || p->n_groups > 64 || p->n_steps < 0 || p->burn_in < 0)
+        return fail(ctx, MRQ_INVALID_ARG, "need n_walkers > 0, 1 <= n_groups <= 64, n_steps >= 0, burn_in >= 0");
+    CK(cudaSetDevice(ctx->device));
+    if (p->n_walkers > ctx->walk_cap) {
+        dfree(ctx->d_walk);
+        CK(cudaMalloc(&ctx->d_walk, sizeof(Walker) * p->n_walkers));
+        ctx->walk_cap = p->n_walkers;
+    }
+    if (ctx->acc_lab != ctx->nlab || ctx->acc_G != p->n_groups) {
+        dfree(ctx->d_accN);
+        dfree(ctx->d_accU);
+        dfree(ctx->d_accW);
+        dfree(ctx->d_accE);
+        dfree(ctx->d_types);
+        CK(cudaMalloc(&ctx->d_accN, sizeof(double) * ctx->nlab * p->n_groups));
+        CK(cudaMalloc(&ctx->d_accU, sizeof(double) * ctx->nlab * p->n_groups));
+        CK(cudaMalloc(&ctx->d_accW, sizeof(double) * p->n_groups));
+        CK(cudaMalloc(&ctx->d_accE, sizeof(double) * p->n_groups));
+        CK(cudaMalloc(&ctx->d_types, sizeof(unsigned long long) * MRQ_NTYPES));
+        ctx->acc_lab = ctx->nlab;
+        ctx->acc_G = p->n_groups;
+    }
+    ctx->nwalk = p->n_walkers;
+    ctx->G = p->n_groups;
+    ctx->burn = p->burn_in;
+    ctx->seed = p->seed;
+    ctx->tau = p->screen_tau;
+    ctx->total_steps = 0;
+    ctx->walk_ms = 0.0;
+    ctx->launches = 0;
+    ctx->launches_total = 0;
+    CK(cudaMemsetAsync(ctx->d_accN, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_accU, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_accW, 0, sizeof(double) * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_accE, 0, sizeof(double) * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_types, 0, sizeof(unsigned long long) * MRQ_NTYPES, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    if (int r = push_sys(ctx)) return r;
+    double c0 = 1.0;
+    CK(cudaMemcpyAsync(&c0, ctx->d_c, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    k_walkers_init<<<(unsigned)((ctx->nwalk + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_walk, ctx->nwalk, ctx->start[0], ctx->start[1], ctx->start[2], ctx->start[3], c0 * ctx->start_c, 0, ctx->G);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!ctx->ref || !ctx->d_walk || ctx->nwalk == 0) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    if (n_steps <= 0) return 0;
+    CK(cudaSetDevice(ctx->device));
+    const unsigned blocks = (unsigned)((ctx->nwalk + 3) / 4);
+    const size_t k = (size_t)ctx->launches * 2;
+    while (ctx->evs.size() < k + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->evs.push_back(e);
+    }
+    CK(cudaEventRecord(ctx->evs[k], ctx->stream));
+    if (ctx->W == 1) k_walk<1><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps);
+    else k_walk<2><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
+    ctx->launches++;
+    ctx->total_steps += n_steps * ctx->nwalk;
+    return 0;
+}
+
+int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
+    if (!ctx || !out) return MRQ_INVALID_ARG;
+    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    CK(cudaSetDevice(ctx->device));
+    const long long chunk = 8192;
+    const int nchunk = (int)((ctx->nlab + chunk - 1) / chunk);
+    const long long need = (long long)(ctx->G + 1) * nchunk * FIN_NV;
+    if (need > ctx->partial_cap) {
+        dfree(ctx->d_partial);
+        CK(cudaMalloc(&ctx->d_partial, sizeof(double) * need));
+        ctx->partial_cap = need;
+    }
+    ctx->hsys.e0 = ctx->e0;
+    if (int r = push_sys(ctx)) return r;
+    k_fin_labels<<<(ctx->G + 1) * nchunk, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->tau, nchunk, chunk, ctx->d_partial);
+    CK(cudaGetLastError());
+    k_fin_reduce<<<1, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->d_partial, nchunk, ctx->d_res);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, ctx->d_res, sizeof(mrq_result), cudaMemcpyDeviceToHost, ctx->stream));
+    int flag = 0;
+    if (int r = check_err_flag(ctx, &flag)) return r;
+    for (int i = 0; i < ctx->launches; i++) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->evs[2 * i], ctx->evs[2 * i + 1]) == cudaSuccess) ctx->walk_ms += ms;
+    }
+    out->walk_launches = ctx->launches_total += ctx->launches;
+    ctx->launches = 0;
+    out->seconds = ctx->walk_ms * 1e-3;
+    out->total_steps = ctx->total_steps;
+    out->status = 0;
+    if (flag & MRQ_ERR_HASH) out->status = MRQ_HASH_OVERFLOW;
+    else if (flag & (MRQ_ERR_NOMOVE | MRQ_ERR_LABEL)) out->status = MRQ_NO_MOVE;
+    if (out->status) return fail(ctx, out->status, "device flagged an error during the walk (flags %d)", flag);
+    return 0;
+}
+
+int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out) {
+    if (int r = mrq_walkers_init(ctx, p)) return r;
+    if (int r = mrq_walkers_advance(ctx, p->n_steps)) return r;
+    return mrq_finalize(ctx, out);
+}
+
+int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW, double* accE, int64_t* type_steps) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!ctx->d_accN) return fail(ctx, MRQ_NOT_LOADED, "no accumulators");
+    CK(cudaSetDevice(ctx->device));
+    const long long L = ctx->nlab * ctx->G;
+    if (accN) CK(cudaMemcpyAsync(accN, ctx->d_accN, sizeof(double) * L, cudaMemcpyDeviceToHost, ctx->stream));
+    if (accU) CK(cudaMemcpyAsync(accU, ctx->d_accU, sizeof(double) * L, cudaMemcpyDeviceToHost, ctx->stream));
+    if (accW) CK(cudaMemcpyAsync(accW, ctx->d_accW, sizeof(double) * ctx->G, cudaMemcpyDeviceToHost, ctx->stream));
+    if (accE) CK(cudaMemcpyAsync(accE, ctx->d_accE, sizeof(double) * ctx->G, cudaMemcpyDeviceToHost, ctx->stream));
+    if (type_steps)
+        CK(cudaMemcpyAsync(type_steps, ctx->d_types, sizeof(int64_t) * MRQ_NTYPES, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    CK(cudaSetDevice(ctx->device));
+    std::vector<Walker> w(ctx->nwalk);
+    CK(cudaMemcpyAsync(w.data(), ctx->d_walk, sizeof(Walker) * ctx->nwalk, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int W = ctx->W;
+    for (long long i = 0; i < ctx->nwalk; i++) {
+        if (dets)
+            for (int k = 0; k < W; k++) {
+                dets[i * 2 * W + k] = w[i].d[0][k];
+                dets[i * 2 * W + W + k] = w[i].d[1][k];
+            }
+        if (psi) psi[i] = w[i].psi;
+    }
+    return 0;
+}
+
+}  // extern "C"
