@@ -197,6 +197,22 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps);
  */
 int mrq_finalize(mrq_ctx* ctx, mrq_result* out);
 
+/*
+ * Same result as mrq_finalize, but the call allocates no device memory: its partial sums go to
+ * a fixed array compiled into the library (MRQ_NOALLOC_SCRATCH_DOUBLES doubles, 4 MiB), which
+ * every GPU that loads the library keeps until the process exits.  For callers that must not
+ * call cudaMalloc/cudaFree while they run, e.g. a serving loop whose device memory is all
+ * handed to its own pool allocator, or a latency-bound loop that cannot absorb the device
+ * synchronisation an allocation may cause.  The paper has no counterpart; it is an
+ * implementation convenience.  The array's device address is looked up in mrq_create, once
+ * per device.  Needs (n_groups + 1) * ceil(n_labels / 8192) * 45 doubles of scratch and
+ * returns MRQ_TOO_LARGE when that exceeds the fixed size.  All calls on one device share the
+ * array (each call overwrites what it uses), so calls whose GPU work overlaps race: issue them
+ * on one stream, or wait for one to finish before the next.
+ */
+#define MRQ_NOALLOC_SCRATCH_DOUBLES (1 << 19)
+int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out);
+
 /* mrq_walkers_init + mrq_walkers_advance(p->n_steps) + mrq_finalize. */
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out);
 

@@ -105,11 +105,13 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_walkers_init.argtypes = [P, C.POINTER(SampleParams)]
     lib.mrq_walkers_advance.argtypes = [P, I64]
     lib.mrq_finalize.argtypes = [P, C.POINTER(Result)]
+    lib.mrq_finalize_noalloc.argtypes = [P, C.POINTER(Result)]
     lib.mrq_sample.argtypes = [P, C.POINTER(SampleParams), C.POINTER(Result)]
     lib.mrq_read_accumulators.argtypes = [P, P, P, P, P, P]
     lib.mrq_read_walkers.argtypes = [P, P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
+               "mrq_finalize_noalloc",
                "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
@@ -226,6 +228,12 @@ class Context:
     def finalize(self) -> dict:
         r = Result()
         self._check(self._lib.mrq_finalize(self._h, C.byref(r)))
+        return r.as_dict()
+
+    def finalize_noalloc(self) -> dict:
+        """mrq_finalize without any device allocation (fixed scratch inside the library)."""
+        r = Result()
+        self._check(self._lib.mrq_finalize_noalloc(self._h, C.byref(r)))
         return r.as_dict()
 
     def sample(self, p: SampleParams) -> dict:

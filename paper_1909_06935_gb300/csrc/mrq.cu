@@ -983,6 +983,17 @@ __global__ void k_fin_reduce(const SysDev* __restrict__ sys, const double* parti
     res->walker_steps = wsteps;
 }
 
+// ============================================================================ fixed scratch for mrq_finalize_noalloc
+//
+// Partial sums of the finalize kernels for callers that cannot allocate device memory.  Every
+// GPU that loads this library holds this array until the process exits.  All calls on a device
+// share it: a call overwrites every slot it reads, and two calls whose kernels overlap on the
+// GPU race on it.
+static __device__ __align__(256) double g_noalloc_scratch[MRQ_NOALLOC_SCRATCH_DOUBLES];
+
+#define MRQ_MAX_DEVICES 64
+static double* g_noalloc_ptr[MRQ_MAX_DEVICES];     // device address of g_noalloc_scratch, per device
+
 // ============================================================================ host runtime
 
 struct mrq_ctx {
@@ -1135,6 +1146,13 @@ int mrq_create(mrq_ctx** out, int device) {
     }
     ctx->own_stream = true;
     cudaMemset(ctx->d_err, 0, sizeof(int));
+    // set-up of the allocation-free finalize: the device address of the fixed scratch array,
+    // looked up once per device with that device current (host code cannot use the symbol itself)
+    if (device >= 0 && device < MRQ_MAX_DEVICES && g_noalloc_ptr[device] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess) g_noalloc_ptr[device] = (double*)p;
+        else cudaGetLastError();
+    }
     *out = ctx;
     return 0;
 }
@@ -1479,23 +1497,20 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     return 0;
 }
 
-int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
-    if (!ctx || !out) return MRQ_INVALID_ARG;
-    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
-    CK(cudaSetDevice(ctx->device));
-    const long long chunk = 8192;
-    const int nchunk = (int)((ctx->nlab + chunk - 1) / chunk);
-    const long long need = (long long)(ctx->G + 1) * nchunk * FIN_NV;
-    if (need > ctx->partial_cap) {
-        dfree(ctx->d_partial);
-        CK(cudaMalloc(&ctx->d_partial, sizeof(double) * need));
-        ctx->partial_cap = need;
-    }
+static const long long FIN_CHUNK = 8192;
+
+static long long fin_scratch_doubles(const mrq_ctx* ctx, int* nchunk) {
+    *nchunk = (int)((ctx->nlab + FIN_CHUNK - 1) / FIN_CHUNK);
+    return (long long)(ctx->G + 1) * (*nchunk) * FIN_NV;
+}
+
+// finalize with the partial sums in `scratch` (at least fin_scratch_doubles() doubles)
+static int finalize_with(mrq_ctx* ctx, mrq_result* out, double* scratch, int nchunk) {
     ctx->hsys.e0 = ctx->e0;
     if (int r = push_sys(ctx)) return r;
-    k_fin_labels<<<(ctx->G + 1) * nchunk, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->tau, nchunk, chunk, ctx->d_partial);
+    k_fin_labels<<<(ctx->G + 1) * nchunk, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->tau, nchunk, FIN_CHUNK, scratch);
     CK(cudaGetLastError());
-    k_fin_reduce<<<1, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->d_partial, nchunk, ctx->d_res);
+    k_fin_reduce<<<1, 256, 0, ctx->stream>>>(ctx->d_sys, scratch, nchunk, ctx->d_res);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, ctx->d_res, sizeof(mrq_result), cudaMemcpyDeviceToHost, ctx->stream));
     int flag = 0;
@@ -1513,6 +1528,36 @@ int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
     else if (flag & (MRQ_ERR_NOMOVE | MRQ_ERR_LABEL)) out->status = MRQ_NO_MOVE;
     if (out->status) return fail(ctx, out->status, "device flagged an error during the walk (flags %d)", flag);
     return 0;
+}
+
+int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
+    if (!ctx || !out) return MRQ_INVALID_ARG;
+    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    CK(cudaSetDevice(ctx->device));
+    int nchunk = 0;
+    const long long need = fin_scratch_doubles(ctx, &nchunk);
+    if (need > ctx->partial_cap) {
+        dfree(ctx->d_partial);
+        CK(cudaMalloc(&ctx->d_partial, sizeof(double) * need));
+        ctx->partial_cap = need;
+    }
+    return finalize_with(ctx, out, ctx->d_partial, nchunk);
+}
+
+int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
+    if (!ctx || !out) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    if (ctx->device < 0 || ctx->device >= MRQ_MAX_DEVICES || g_noalloc_ptr[ctx->device] == nullptr)
+        return fail(ctx, MRQ_CUDA_ERROR, "fixed finalize scratch has no device address on device %d", ctx->device);
+    int nchunk = 0;
+    const long long need = fin_scratch_doubles(ctx, &nchunk);
+    if (need > MRQ_NOALLOC_SCRATCH_DOUBLES)
+        return fail(ctx, MRQ_TOO_LARGE,
+                    "mrq_finalize_noalloc: %lld labels x %d groups need %lld scratch doubles, more than its fixed "
+                    "%d (use mrq_finalize)", (long long)ctx->nlab, ctx->G, need, MRQ_NOALLOC_SCRATCH_DOUBLES);
+    CK(cudaSetDevice(ctx->device));
+    return finalize_with(ctx, out, g_noalloc_ptr[ctx->device], nchunk);
 }
 
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out) {
