@@ -111,10 +111,11 @@ def dist_env():
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(system, seconds: float, threads: int):
+def cpu_oracle_rate(system, seconds: float, threads: int, orc=None):
     """Walker-steps/s of the plain C oracle's walk on a bounded sample of the same workload."""
     import oracle as O
-    orc = O.Oracle.from_system(system)
+    if orc is None:
+        orc = O.Oracle.from_system(system)
     nw = max(threads, 1)
     t0 = time.perf_counter()
     acc = orc.sample(nw, 1, 0, seed=3, n_groups=1, threads=threads)
@@ -133,14 +134,16 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
+    import oracle as O
     import synthetic as S
     system = S.workload(WORKLOAD)
     threads = os.cpu_count() or 1
+    orc = O.Oracle.from_system(system)
     per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
     rates = []
     meta = None
     for k in range(args.warmup + args.steps):
-        r, meta = cpu_oracle_rate(system, per_step, threads)
+        r, meta = cpu_oracle_rate(system, per_step, threads, orc)
         if k >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)

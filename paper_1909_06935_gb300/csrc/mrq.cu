@@ -46,7 +46,10 @@ __constant__ unsigned char c_pair_b[6] = {0, 1, 2, 1, 2, 2};
 
 __device__ __forceinline__ int pairs_of(int k1, int k2, bool same) { return same ? k1 * (k1 - 1) / 2 : k1 * k2; }
 
-// decode a pair index inside one class (triangular, i < j) or across two classes
+// enumeration speed of an orbital class: active slowest (0), core (1), virtual fastest (2)
+__device__ __forceinline__ int cls_pri(int c) { return c == 1 ? 0 : (c == 0 ? 1 : 2); }
+
+// pair index -> (i < j), ordered by j then i (used for the occupied-pair diagonal sums)
 __device__ __forceinline__ void tri_decode(int op, int& i, int& j) {
     int jj = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)op)) * 0.5f);
     while (jj * (jj - 1) / 2 > op) jj--;
@@ -98,6 +101,7 @@ __device__ void build_lists(const SysDev& S, const unsigned long long (&d)[2][W]
     for (int base = 0; base < MRQ_MAXB; base += 32) {
         int ci = base + lane;
         int size = 0, kind = 0, sg = 0, X1 = 0, X2 = 0, Y1 = 0, Y2 = 0;
+        unsigned order = 0;
         if (ci < MRQ_MAXB) {
             if (ci < 18) {
                 kind = 0; sg = ci / 9; X1 = (ci % 9) / 3; Y1 = ci % 3;
@@ -115,6 +119,23 @@ __device__ void build_lists(const SysDev& S, const unsigned long long (&d)[2][W]
                 kind = 2; X1 = c / 27; Y1 = (c / 9) % 3; X2 = (c / 3) % 3; Y2 = c % 3;
                 size = (sh.os[0][X1 + 1] - sh.os[0][X1]) * (sh.es[0][Y1 + 1] - sh.es[0][Y1]) *
                        (sh.os[1][X2 + 1] - sh.os[1][X2]) * (sh.es[1][Y2 + 1] - sh.es[1][Y2]);
+            }
+            // digit order inside the block: active indices slowest, core next, virtual fastest, so
+            // that the lanes of one warp iteration share the active remnant of their neighbours
+            if (kind == 0) {
+                order = cls_pri(X1) > cls_pri(Y1) ? 1u : 0u;                         // occ fastest?
+            } else if (kind == 1) {
+                int po = min(cls_pri(X1), cls_pri(X2)), pe = min(cls_pri(Y1), cls_pri(Y2));
+                order = (pe < po ? 1u : 0u) | ((X1 != X2 && cls_pri(X1) > cls_pri(X2)) ? 2u : 0u) |
+                        ((Y1 != Y2 && cls_pri(Y1) > cls_pri(Y2)) ? 4u : 0u);
+            } else {
+                int cl[4] = {X1, Y1, X2, Y2}, perm[4] = {0, 1, 2, 3};
+                for (int a = 1; a < 4; a++)       // stable insertion sort by class priority
+                    for (int b2 = a; b2 > 0 && cls_pri(cl[perm[b2]]) < cls_pri(cl[perm[b2 - 1]]); b2--) {
+                        int t = perm[b2]; perm[b2] = perm[b2 - 1]; perm[b2 - 1] = t;
+                    }
+                order = (unsigned)perm[0] | ((unsigned)perm[1] << 2) | ((unsigned)perm[2] << 4) |
+                        ((unsigned)perm[3] << 6);
             }
             int dh = (X1 == 0) - (Y1 == 0), dp = (Y1 == 2) - (X1 == 2);
             if (kind != 0) {
@@ -134,7 +155,7 @@ __device__ void build_lists(const SysDev& S, const unsigned long long (&d)[2][W]
         if (size > 0) {
             int k = run + __popc(vm & ((1u << lane) - 1u));
             sh.bdesc[k] = (unsigned)kind | ((unsigned)sg << 2) | ((unsigned)X1 << 4) | ((unsigned)X2 << 6) |
-                          ((unsigned)Y1 << 8) | ((unsigned)Y2 << 10);
+                          ((unsigned)Y1 << 8) | ((unsigned)Y2 << 10) | (order << 12);
             sh.bstart[k + 1] = carry + x;
         }
         carry += __shfl_sync(0xffffffffu, x, 31);
@@ -147,43 +168,65 @@ __device__ void build_lists(const SysDev& S, const unsigned long long (&d)[2][W]
     __syncwarp();
 }
 
+// pair index -> (i < j) in lexicographic order (i slowest, j fastest) among k items
+__device__ __forceinline__ void lex_decode(int op, int k, int& i, int& j) {
+    int ti, tj;
+    tri_decode(k * (k - 1) / 2 - 1 - op, ti, tj);
+    i = k - 1 - tj;
+    j = k - 1 - ti;
+}
+
+// pair within one class (lexicographic) or across two classes (rev: first index fastest)
+__device__ __forceinline__ void pair_decode(int op, bool same, int k1, int k2, bool rev, int& i, int& j) {
+    if (same) lex_decode(op, k1, i, j);
+    else if (rev) { j = op / k1; i = op - j * k1; }
+    else { i = op / k2; j = op - i * k2; }
+}
+
 // decode neighbour `loc` of block `desc` into removed r1<=r2 and added a1<=a2 spin orbitals
 __device__ __forceinline__ void decode_exc(const WarpSh& sh, int n, unsigned desc, int loc, int& kind, int& r1,
                                            int& r2, int& a1, int& a2) {
     kind = desc & 3;
     int sg = (desc >> 2) & 1, X1 = (desc >> 4) & 3, X2 = (desc >> 6) & 3, Y1 = (desc >> 8) & 3,
         Y2 = (desc >> 10) & 3;
+    const unsigned order = desc >> 12;
     if (kind == 0) {
-        int nY = sh.es[sg][Y1 + 1] - sh.es[sg][Y1];
-        int i = loc / nY, a = loc - i * nY;
+        int nX = sh.os[sg][X1 + 1] - sh.os[sg][X1], nY = sh.es[sg][Y1 + 1] - sh.es[sg][Y1];
+        int i, a;
+        if (order & 1u) { a = loc / nX; i = loc - a * nX; }
+        else { i = loc / nY; a = loc - i * nY; }
         r1 = r2 = sg * n + sh.ol[sg][sh.os[sg][X1] + i];
         a1 = a2 = sg * n + sh.el[sg][sh.es[sg][Y1] + a];
     } else if (kind == 1) {
-        int k2 = sh.os[sg][X2 + 1] - sh.os[sg][X2];
+        int k1 = sh.os[sg][X1 + 1] - sh.os[sg][X1], k2 = sh.os[sg][X2 + 1] - sh.os[sg][X2];
         int e1 = sh.es[sg][Y1 + 1] - sh.es[sg][Y1], e2 = sh.es[sg][Y2 + 1] - sh.es[sg][Y2];
-        int nEP = pairs_of(e1, e2, Y1 == Y2);
-        int op = loc / nEP, ep = loc - op * nEP;
+        int nOP = pairs_of(k1, k2, X1 == X2), nEP = pairs_of(e1, e2, Y1 == Y2);
+        int op, ep;
+        if (order & 1u) { ep = loc / nOP; op = loc - ep * nOP; }
+        else { op = loc / nEP; ep = loc - op * nEP; }
         int i, j, a, b;
-        if (X1 == X2) tri_decode(op, i, j);
-        else { i = op / k2; j = op - i * k2; }
-        if (Y1 == Y2) tri_decode(ep, a, b);
-        else { a = ep / e2; b = ep - a * e2; }
+        pair_decode(op, X1 == X2, k1, k2, (order & 2u) != 0, i, j);
+        pair_decode(ep, Y1 == Y2, e1, e2, (order & 4u) != 0, a, b);
         r1 = sg * n + sh.ol[sg][sh.os[sg][X1] + i];
         r2 = sg * n + sh.ol[sg][sh.os[sg][X2] + j];
         a1 = sg * n + sh.el[sg][sh.es[sg][Y1] + a];
         a2 = sg * n + sh.el[sg][sh.es[sg][Y2] + b];
     } else {
-        int nYa = sh.es[0][Y1 + 1] - sh.es[0][Y1];
-        int nYb = sh.es[1][Y2 + 1] - sh.es[1][Y2];
-        int nXb = sh.os[1][X2 + 1] - sh.os[1][X2];
-        int nbeta = nXb * nYb;
-        int sa = loc / nbeta, sb = loc - sa * nbeta;
-        int ia = sa / nYa, aa = sa - ia * nYa;
-        int ib = sb / nYb, ab = sb - ib * nYb;
-        r1 = sh.ol[0][sh.os[0][X1] + ia];
-        a1 = sh.el[0][sh.es[0][Y1] + aa];
-        r2 = n + sh.ol[1][sh.os[1][X2] + ib];
-        a2 = n + sh.el[1][sh.es[1][Y2] + ab];
+        // digits 0: alpha occupied (X1), 1: alpha empty (Y1), 2: beta occupied (X2), 3: beta empty (Y2)
+        int rad[4] = {sh.os[0][X1 + 1] - sh.os[0][X1], sh.es[0][Y1 + 1] - sh.es[0][Y1],
+                      sh.os[1][X2 + 1] - sh.os[1][X2], sh.es[1][Y2 + 1] - sh.es[1][Y2]};
+        int x[4];
+#pragma unroll
+        for (int d = 3; d >= 0; d--) {
+            int id = (order >> (2 * d)) & 3u;
+            int q = loc / rad[id];
+            x[id] = loc - q * rad[id];
+            loc = q;
+        }
+        r1 = sh.ol[0][sh.os[0][X1] + x[0]];
+        a1 = sh.el[0][sh.es[0][Y1] + x[1]];
+        r2 = n + sh.ol[1][sh.os[1][X2] + x[2]];
+        a2 = n + sh.el[1][sh.es[1][Y2] + x[3]];
     }
 }
 
@@ -242,8 +285,121 @@ struct LocalOut {
     int nnb;
 };
 
-// One local evaluation at det n (walker) with amplitude psin.  In MODE_STEP also picks the move;
-// in MODE_DEBUG writes neighbour records.  Returns the quantities on every lane.
+// per-lane partial results of one local evaluation
+template <int W>
+struct LaneAcc {
+    double sS, sH, sHD;
+    double bt;          // best (smallest) exponential clock
+    float btf;          // its FP32 image, for screening
+    unsigned bexc;
+    double bpsi;
+    unsigned long long bm[2][W];
+};
+
+template <int W>
+__device__ __forceinline__ void lane_acc_init(LaneAcc<W>& a, const unsigned long long (&n)[2][W]) {
+    a.sS = a.sH = a.sHD = 0.0;
+    a.bt = INFINITY;
+    a.btf = INFINITY;
+    a.bexc = 0xFFFFFFFFu;
+    a.bpsi = 0.0;
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+        for (int w = 0; w < W; w++) a.bm[sg][w] = n[sg][w];
+}
+
+// rates, local sums and the move race for one neighbour m (Eq. 5, Eq. 16, Sec. II B)
+template <int W, int MODE>
+__device__ __forceinline__ void lane_post(const SysDev& S, LaneAcc<W>& a, const unsigned long long (&m)[2][W],
+                                          double hnm, double hd, bool same_label, double om, double psim,
+                                          double inv_psin, unsigned exc, unsigned step, unsigned wid,
+                                          mrq_neighbour* rec) {
+    const double ratio = psim * inv_psin;
+    const double g = fabs(hnm * ratio);
+    a.sS += g;
+    a.sH += hnm * ratio;
+    if (same_label) a.sHD += hd * ratio;
+    if (MODE == MODE_STEP) {
+        if (g > 0.0) {
+            // exact FP64 clock only where a cheap FP32 bound says it can win
+            const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
+            const float tf = race_clock_f32(k53, (float)g);
+            if (!(tf > a.btf * 1.0001f)) {
+                const double t = race_clock_f64(k53, g);
+                if (t < a.bt || (t == a.bt && exc < a.bexc)) {
+                    a.btf = (float)t;
+                    a.bt = t;
+                    a.bexc = exc;
+                    a.bpsi = psim;
+#pragma unroll
+                    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+                        for (int w = 0; w < W; w++) a.bm[sg][w] = m[sg][w];
+                }
+            }
+        }
+    } else if (rec != nullptr) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) rec->det[w] = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            rec->det[w] = m[0][w];
+            rec->det[W + w] = m[1][w];
+        }
+        rec->h = hnm;
+        rec->hd = same_label ? hd : 0.0;
+        rec->o = om;
+        rec->psi = psim;
+        rec->gamma = g;
+        rec->exc = exc;
+        rec->pad = 0;
+    }
+}
+
+// warp reductions, diagonals, and (MODE_STEP) the winning move
+template <int W, int MODE>
+__device__ LocalOut finish_local(const SysDev& S, const WarpSh& sh, const unsigned long long (&n)[2][W],
+                                 long long ln, int lane, LaneAcc<W>& a, int total,
+                                 unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc) {
+    LocalOut out;
+    out.S = warp_sum(a.sS);
+    const double eh = warp_sum(a.sH);
+    const double ehd = warp_sum(a.sHD);
+    double hnn, hdnn;
+    diagonals<W>(S, sh, n, lane, hnn, hdnn);
+    out.hnn = hnn;
+    out.hdnn = hdnn;
+    out.EL = hnn + eh;
+    out.num = ln > 0 ? hdnn + ehd : 0.0;
+    out.nnb = total;
+    if (MODE == MODE_STEP) {
+        double t = a.bt;
+        unsigned e = a.bexc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double t2 = __shfl_xor_sync(0xffffffffu, t, o);
+            unsigned e2 = __shfl_xor_sync(0xffffffffu, e, o);
+            if (t2 < t || (t2 == t && e2 < e)) {
+                t = t2;
+                e = e2;
+            }
+        }
+        unsigned win = __ballot_sync(0xffffffffu, a.bexc == e && a.bt == t);
+        int src = win ? __ffs(win) - 1 : 0;
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) best[sg][w] = __shfl_sync(0xffffffffu, a.bm[sg][w], src);
+        best_psi = __shfl_sync(0xffffffffu, a.bpsi, src);
+        best_exc = e;
+    }
+    return out;
+}
+
+// Generic local evaluation at det n (any class) with amplitude psin: one lane per neighbour in
+// the class-block enumeration, reach-back per lane.  MODE_STEP also picks the move; MODE_DEBUG
+// writes neighbour records.  Returns the quantities on every lane.
 template <int W, int MODE, class C>
 __device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long long (&n)[2][W], double psin,
                                long long ln, int h, int p, unsigned step, unsigned wid, int lane,
@@ -253,16 +409,12 @@ __device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long 
     const int total = sh.bstart[sh.nb];
     const double c0 = __ldg(S.c);
     const double inv_psin = psin != 0.0 ? 1.0 / psin : 0.0;   // zero-amplitude determinants: ratios 0
-    double sS = 0.0, sH = 0.0, sHD = 0.0;
-    double bt = INFINITY;
-    float btf = INFINITY;
-    unsigned bexc = 0xFFFFFFFFu;
-    double bpsi = 0.0;
-    unsigned long long bm[2][W];
-#pragma unroll
-    for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-        for (int w = 0; w < W; w++) bm[sg][w] = n[sg][w];
+    // a CAS walker is itself one reach-back candidate of each of its FOIS neighbours
+    const unsigned long long self_key =
+        ln == 0 ? hash_key(S, active_bits<W>(S, n[0]), active_bits<W>(S, n[1])) : MRQ_EMPTY_KEY;
+    const double phi_self = ln == 0 ? psin / c0 : 0.0;
+    LaneAcc<W> acc;
+    lane_acc_init<W>(acc, n);
     int b = 0;
     for (int idx = lane; idx < total; idx += 32) {
         while (idx >= sh.bstart[b + 1]) b++;
@@ -294,103 +446,50 @@ __device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long 
             om = hash_lookup(S, hash_key(S, active_bits<W>(S, m[0]), active_bits<W>(S, m[1])), ctr);
             psim = c0 * om;
         } else {
-            om = reach_back<W>(S, m, ctr);
+            om = reach_back<W>(S, m, ctr, self_key, hnm * phi_self);
             ctr.g();
             psim = __ldg(S.c + lm) * om;
         }
-        const double ratio = psim * inv_psin;
-        const double g = fabs(hnm * ratio);
-        sS += g;
-        sH += hnm * ratio;
-        double hd = 0.0;
-        if (ln > 0 && active_only(desc)) {
-            hd = (kind == 0) ? hd_single_elem<W>(S, n, r1, a1, ctr) : hnm;
-            sHD += hd * ratio;
-        }
+        const bool same = ln > 0 && active_only(desc);
+        const double hd = same ? ((kind == 0) ? hd_single_elem<W>(S, n, r1, a1, ctr) : hnm) : 0.0;
         const unsigned exc = (unsigned)r1 | ((unsigned)r2 << 8) | ((unsigned)a1 << 16) | ((unsigned)a2 << 24);
-        if (MODE == MODE_STEP) {
-            if (g > 0.0) {
-                // exact FP64 clock only where a cheap FP32 bound says it can win
-                const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
-                const float tf = race_clock_f32(k53, (float)g);
-                if (!(tf > btf * 1.0001f)) {
-                    const double t = race_clock_f64(k53, g);
-                    if (t < bt || (t == bt && exc < bexc)) {
-                        btf = (float)t;
-                        bt = t;
-                        bexc = exc;
-                        bpsi = psim;
-#pragma unroll
-                        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-                            for (int w = 0; w < W; w++) bm[sg][w] = m[sg][w];
-                    }
-                }
-            }
-        } else {
-            if (nbout != nullptr && idx < max_nb) {
-                mrq_neighbour& r = nbout[idx];
-#pragma unroll
-                for (int w = 0; w < 4; w++) r.det[w] = 0;
-#pragma unroll
-                for (int w = 0; w < W; w++) {
-                    r.det[w] = m[0][w];
-                    r.det[W + w] = m[1][w];
-                }
-                r.h = hnm;
-                r.hd = hd;
-                r.o = om;
-                r.psi = psim;
-                r.gamma = g;
-                r.exc = exc;
-                r.pad = 0;
-            }
-        }
+        lane_post<W, MODE>(S, acc, m, hnm, hd, same, om, psim, inv_psin, exc, step, wid,
+                           (MODE == MODE_DEBUG && nbout != nullptr && idx < max_nb) ? nbout + idx : nullptr);
     }
-    LocalOut out;
-    out.S = warp_sum(sS);
-    const double eh = warp_sum(sH);
-    const double ehd = warp_sum(sHD);
-    double hnn, hdnn;
-    diagonals<W>(S, sh, n, lane, hnn, hdnn);
-    out.hnn = hnn;
-    out.hdnn = hdnn;
-    out.EL = hnn + eh;
-    out.num = ln > 0 ? hdnn + ehd : 0.0;
-    out.nnb = total;
-    if (MODE == MODE_STEP) {
-        // warp argmin over (clock, exc)
-        double t = bt;
-        unsigned e = bexc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double t2 = __shfl_xor_sync(0xffffffffu, t, o);
-            unsigned e2 = __shfl_xor_sync(0xffffffffu, e, o);
-            if (t2 < t || (t2 == t && e2 < e)) {
-                t = t2;
-                e = e2;
-            }
-        }
-        unsigned win = __ballot_sync(0xffffffffu, bexc == e && bt == t);
-        int src = win ? __ffs(win) - 1 : 0;
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-            for (int w = 0; w < W; w++) best[sg][w] = __shfl_sync(0xffffffffu, bm[sg][w], src);
-        best_psi = __shfl_sync(0xffffffffu, bpsi, src);
-        best_exc = e;
-    }
-    return out;
+    return finish_local<W, MODE>(S, sh, n, ln, lane, acc, total, best, best_psi, best_exc);
+}
+
+#include "mrq_cas.cuh"
+
+#ifndef MRQ_WALK_MIN_BLOCKS
+#define MRQ_WALK_MIN_BLOCKS 2
+#endif
+
+// per-warp shared memory: WarpSh, then the CAS path's candidate list (phi0 values and codes)
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int cap) {
+    const size_t a = (sizeof(WarpSh) + 15) / 16 * 16;
+    return a + (size_t)cap * sizeof(double) + ((size_t)cap * sizeof(unsigned) + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ void warp_smem(unsigned char* base, int cap, WarpSh*& sh, double*& cphi, unsigned*& ccode) {
+    sh = reinterpret_cast<WarpSh*>(base);
+    cphi = reinterpret_cast<double*>(base + (sizeof(WarpSh) + 15) / 16 * 16);
+    ccode = reinterpret_cast<unsigned*>(cphi + cap);
 }
 
 template <int W>
-__global__ void __launch_bounds__(128) k_walk(const SysDev* __restrict__ systems, Walker* __restrict__ walkers,
-                                              long long nslots, int nsteps) {
-    __shared__ WarpSh shs[4];
+__global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev* __restrict__ systems,
+                                                                   Walker* __restrict__ walkers, long long nslots,
+                                                                   int nsteps, int cap) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long slot = (long long)blockIdx.x * 4 + wi;
     if (slot >= nslots) return;
-    WarpSh& sh = shs[wi];
+    WarpSh* shp;
+    double* cphi;
+    unsigned* ccode;
+    warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
+    WarpSh& sh = *shp;
     Walker wk = walkers[slot];
     const SysDev S = systems[wk.sys];
     unsigned long long n[2][W];
@@ -406,8 +505,13 @@ __global__ void __launch_bounds__(128) k_walk(const SysDev* __restrict__ systems
         double npsi = 0.0;
         unsigned nexc = 0;
         NoCtr nc;
-        LocalOut lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc,
+        LocalOut lo;
+        if (ln == 0)
+            lo = local_eval_cas<W, MODE_STEP>(S, sh, cphi, ccode, n, psin, wk.step, wk.wid, lane, nxt, npsi, nexc,
                                               nullptr, 0, nc);
+        else
+            lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc, nullptr,
+                                          0, nc);
         if (!(lo.S > 0.0) || ln < 0) {
             if (lane == 0) atomicOr(S.err, ln < 0 ? MRQ_ERR_LABEL : MRQ_ERR_NOMOVE);
             break;
@@ -441,16 +545,21 @@ __global__ void __launch_bounds__(128) k_walk(const SysDev* __restrict__ systems
     }
 }
 
-// local quantities of arbitrary determinants (parity)
+// local quantities of arbitrary determinants (parity); CAS determinants take the same grouped
+// path as the walk
 template <int W>
 __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, const unsigned long long* __restrict__ dets,
                                                long long ndet, mrq_local* __restrict__ out, long long max_nb,
-                                               mrq_neighbour* __restrict__ nb) {
-    __shared__ WarpSh shs[4];
+                                               mrq_neighbour* __restrict__ nb, int cap) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long i = (long long)blockIdx.x * 4 + wi;
     if (i >= ndet) return;
-    WarpSh& sh = shs[wi];
+    WarpSh* shp;
+    double* cphi;
+    unsigned* ccode;
+    warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
+    WarpSh& sh = *shp;
     const SysDev S = *sys;
     unsigned long long n[2][W];
 #pragma unroll
@@ -477,8 +586,13 @@ __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, c
     double dpsi;
     unsigned dexc;
     Ctr ctr;
-    LocalOut lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc,
-                                           nb ? nb + i * max_nb : nullptr, max_nb, ctr);
+    mrq_neighbour* rec = nb ? nb + i * max_nb : nullptr;
+    LocalOut lo;
+    if (ln == 0 && psin != 0.0)
+        lo = local_eval_cas<W, MODE_DEBUG>(S, sh, cphi, ccode, n, psin, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb,
+                                           ctr);
+    else
+        lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb, ctr);
     unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -570,6 +684,21 @@ __global__ void k_hash_clear(HashSlot* hash, unsigned long long cap) {
     if (i < cap) {
         hash[i].key = MRQ_EMPTY_KEY;
         hash[i].val = 0.0;
+    }
+}
+
+// half-unpacked integral table E[P(p,q)][r][s] from the 8-fold packed input
+__global__ void k_expand_eri(const double* __restrict__ eri, double* __restrict__ eri4, int n) {
+    const long long npair = (long long)n * (n + 1) / 2;
+    const long long total = npair * n * n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long P = t / ((long long)n * n);
+        int rs = (int)(t - P * n * n);
+        int r = rs / n, s = rs - r * n;
+        long long Q = r >= s ? (long long)r * (r + 1) / 2 + s : (long long)s * (s + 1) / 2 + r;
+        long long i = P >= Q ? P * (P + 1) / 2 + Q : Q * (Q + 1) / 2 + P;
+        eri4[t] = eri[i];
     }
 }
 
@@ -1006,7 +1135,8 @@ struct mrq_ctx {
     int n = 0, nc = 0, na = 0, nv = 0, W = 1, nalpha = 0, nbeta = 0;
     double e_nuc = 0.0;
     long long neri = 0;
-    double *d_h1 = nullptr, *d_eri = nullptr, *d_hc = nullptr, *d_eps = nullptr, *d_gamma = nullptr;
+    double *d_h1 = nullptr, *d_eri = nullptr, *d_eri4 = nullptr, *d_hc = nullptr, *d_eps = nullptr,
+           *d_gamma = nullptr;
     long long nHs = 0, nPs = 0, nlab = 0;
     // reference
     bool ref = false;
@@ -1090,6 +1220,7 @@ static void free_walkers(mrq_ctx* c) {
 static void free_hamiltonian(mrq_ctx* c) {
     dfree(c->d_h1);
     dfree(c->d_eri);
+    dfree(c->d_eri4);
     dfree(c->d_hc);
     dfree(c->d_eps);
     dfree(c->d_gamma);
@@ -1223,6 +1354,7 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     ctx->nlab = ctx->nHs * ctx->nPs;
     CK(cudaMalloc(&ctx->d_h1, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eri, sizeof(double) * ctx->neri));
+    CK(cudaMalloc(&ctx->d_eri4, sizeof(double) * npair * n * n));
     CK(cudaMalloc(&ctx->d_hc, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eps, sizeof(double) * n));
     CK(cudaMalloc(&ctx->d_gamma, sizeof(double) * std::max(1, n_act * n_act)));
@@ -1249,13 +1381,34 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
         }
     }
     s.eri = ctx->d_eri;
+    s.eri4 = ctx->d_eri4;
     s.h1 = ctx->d_h1;
     s.hc = ctx->d_hc;
     s.eps = ctx->d_eps;
     s.e_nuc = e_core;
     s.max_probe = 64;
     s.G = 1;
+    {
+        // largest candidate list of one group of the CAS path: |R'| = rr - p active electrons and
+        // |A'| = rr - h active holes of a remnant with at most N_act + 2 electrons / holes
+        auto nsub_h = [](long long k, int size) { return size == 0 ? 1LL : (size == 1 ? k : k * (k - 1) / 2); };
+        const int nact_e = (n_alpha - n_core) + (n_beta - n_core);
+        const long long amax = std::min(2 * n_act, nact_e + 2), emax = std::min(2 * n_act, 2 * n_act - nact_e + 2);
+        long long cap = 1;
+        for (int hc = 0; hc <= 2; hc++)
+            for (int pc = 0; pc <= 2; pc++) {
+                if (hc == 0 && pc == 0) continue;
+                long long t = nsub_h(amax, 2 - pc) * nsub_h(emax, 2 - hc);
+                if (hc <= 1 && pc <= 1) t += nsub_h(amax, 1 - pc) * nsub_h(emax, 1 - hc);
+                cap = std::max(cap, t);
+            }
+        s.cand_cap = (int)cap;
+        if (4 * warp_smem_bytes(s.cand_cap) > 200 * 1024)
+            return fail(ctx, MRQ_TOO_LARGE, "active space too large for the shared-memory candidate lists");
+    }
     if (int r = push_sys(ctx)) return r;
+    k_expand_eri<<<1216, 256, 0, ctx->stream>>>(ctx->d_eri, ctx->d_eri4, n);
+    CK(cudaGetLastError());
     k_core_fock<<<(n * n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hc);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1410,8 +1563,15 @@ int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* lo
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     if (int r = push_sys(ctx)) return r;
     const unsigned blocks = (unsigned)((n + 3) / 4);
-    if (W == 1) k_debug<1><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb);
-    else k_debug<2><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb);
+    const int cap = ctx->hsys.cand_cap;
+    const size_t smem = 4 * warp_smem_bytes(cap);
+    if (W == 1) {
+        CK(cudaFuncSetAttribute(k_debug<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_debug<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap);
+    } else {
+        CK(cudaFuncSetAttribute(k_debug<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_debug<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(local, d_loc, sizeof(mrq_local) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (nb) CK(cudaMemcpyAsync(nb, d_nb, sizeof(mrq_neighbour) * n * max_nb, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1421,6 +1581,7 @@ int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* lo
     cudaFree(d_loc);
     if (d_nb) cudaFree(d_nb);
     if (flag & MRQ_ERR_HASH) return fail(ctx, MRQ_HASH_OVERFLOW, "hash probe bound exceeded");
+    if (flag & MRQ_ERR_CAP) return fail(ctx, MRQ_TOO_LARGE, "candidate list capacity exceeded");
     return 0;
 }
 
@@ -1488,8 +1649,15 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
         ctx->evs.push_back(e);
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
-    if (ctx->W == 1) k_walk<1><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps);
-    else k_walk<2><<<blocks, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps);
+    const int cap = ctx->hsys.cand_cap;
+    const size_t smem = 4 * warp_smem_bytes(cap);
+    if (ctx->W == 1) {
+        CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, cap);
+    } else {
+        CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, cap);
+    }
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
     ctx->launches++;
@@ -1525,6 +1693,7 @@ static int finalize_with(mrq_ctx* ctx, mrq_result* out, double* scratch, int nch
     out->total_steps = ctx->total_steps;
     out->status = 0;
     if (flag & MRQ_ERR_HASH) out->status = MRQ_HASH_OVERFLOW;
+    else if (flag & MRQ_ERR_CAP) out->status = MRQ_TOO_LARGE;
     else if (flag & (MRQ_ERR_NOMOVE | MRQ_ERR_LABEL)) out->status = MRQ_NO_MOVE;
     if (out->status) return fail(ctx, out->status, "device flagged an error during the walk (flags %d)", flag);
     return 0;

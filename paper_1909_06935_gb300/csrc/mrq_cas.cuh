@@ -1,0 +1,429 @@
+// Local evaluation at a CAS walker, organised by active remnant (included by mrq.cu).
+//
+// Every neighbour m of a CAS determinant n is n with active electrons X_a -> active holes Y_a
+// and core electrons X_c -> virtual orbitals Y_v (|X_a|+|X_c| = |Y_a|+|Y_v| <= 2).  Its reach-back
+// candidates k (Eq. 6-7: the reference determinants H-connected to m) are
+//     k = m - (Y_v u R') + (X_c u A'),   R' active electrons of m, A' active holes of m,
+// and which (R', A') occur, and phi0(k), depend only on the active remnant A_m = A_n - X_a + Y_a and
+// on the counts and spins of X_c and Y_v - not on which core / virtual orbitals they are.  So the
+// neighbours are processed in groups (X_a, Y_a, spins of X_c and Y_v): the warp builds the group's
+// candidate list once (lanes probe distinct keys in parallel, compacted into shared memory), then
+// the lanes run over the group's core / virtual orbital choices and evaluate
+//     O(m) = H_nm phi0(n) + sum_{k in list} <m|H|k> phi0(k)
+// in lockstep; the k = n term needs no lookup.  Every neighbour and every candidate of the plain
+// enumeration is visited exactly once, so the sums are the same as in local_eval.
+
+__device__ __forceinline__ int nsub(int cnt, int size) {
+    return size == 0 ? 1 : (size == 1 ? cnt : cnt * (cnt - 1) / 2);
+}
+
+// position of the k-th (0-based) set bit of a 64-bit mask
+__device__ __forceinline__ int nth_bit64(unsigned long long m, int k) {
+    for (int i = 0; i < k; i++) m &= m - 1;
+    return __ffsll(m) - 1;
+}
+
+// the idx-th subset of `size` (0..2) set bits of m (cnt = popcount of m), lexicographic
+__device__ __forceinline__ unsigned long long subset_bits(unsigned long long m, int cnt, int size, int idx) {
+    if (size == 0) return 0ull;
+    if (size == 1) return 1ull << nth_bit64(m, idx);
+    int i, j;
+    lex_decode(idx, cnt, i, j);
+    return (1ull << nth_bit64(m, i)) | (1ull << nth_bit64(m, j));
+}
+
+// combined active bit (alpha bits 0..31, beta 32..63) -> spin orbital
+__device__ __forceinline__ int act_so(const SysDev& S, int b) { return (b >= 32 ? S.n : 0) + S.nc + (b & 31); }
+
+// up to two set bits of a combined active mask as sorted spin orbitals (returns the count)
+__device__ __forceinline__ int act_list(const SysDev& S, unsigned long long bits, int* out) {
+    int k = 0;
+    while (bits) {
+        int b = __ffsll(bits) - 1;
+        bits &= bits - 1;
+        out[k++] = act_so(S, b);
+    }
+    return k;
+}
+
+// number of choices of `cnt` orbitals of one space (size m) with `nal` of them alpha
+__device__ __forceinline__ int shape_count(int m, int cnt, int nal) {
+    if (cnt == 0) return 1;
+    if (cnt == 1) return m;
+    return nal == 1 ? m * m : m * (m - 1) / 2;
+}
+
+// idx-th choice of that shape as sorted spin orbitals; orbitals of the space start at `off`
+__device__ __forceinline__ void shape_decode(const SysDev& S, int m, int cnt, int nal, int off, int idx, int* out) {
+    if (cnt == 1) {
+        out[0] = (nal ? 0 : S.n) + off + idx;
+    } else if (cnt == 2) {
+        if (nal == 1) {
+            int i = idx / m, j = idx - i * m;
+            out[0] = off + i;
+            out[1] = S.n + off + j;
+        } else {
+            int i, j;
+            lex_decode(idx, m, i, j);
+            const int base = (nal == 2 ? 0 : S.n) + off;
+            out[0] = base + i;
+            out[1] = base + j;
+        }
+    }
+}
+
+__device__ __forceinline__ void sort2(int* x, int k) {
+    if (k == 2 && x[0] > x[1]) {
+        int t = x[0];
+        x[0] = x[1];
+        x[1] = t;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void apply_exc(unsigned long long (&m)[2][W], const SysDev& S, const int* rem,
+                                          const int* add, int k) {
+    for (int i = 0; i < k; i++) {
+        int s1 = rem[i] >= S.n, s2 = add[i] >= S.n;
+        flip<W>(m[s1], rem[i] - s1 * S.n);
+        flip<W>(m[s2], add[i] - s2 * S.n);
+    }
+}
+
+// candidate code: R' and A' as combined active bit positions (7 bits each, 127 = none) and the order
+#define MRQ_NONE 127u
+__device__ __forceinline__ unsigned pack_cand(unsigned long long R, unsigned long long A, int rr) {
+    unsigned p[4] = {MRQ_NONE, MRQ_NONE, MRQ_NONE, MRQ_NONE};
+    int k = 0;
+    while (R) { p[k++] = (unsigned)(__ffsll(R) - 1); R &= R - 1; }
+    k = 2;
+    while (A) { p[k++] = (unsigned)(__ffsll(A) - 1); A &= A - 1; }
+    return p[0] | (p[1] << 7) | (p[2] << 14) | (p[3] << 21) | ((unsigned)(rr - 1) << 28);
+}
+
+// flip the sign of x when the low bit of `odd` is set (exact, no floating-point operation)
+__device__ __forceinline__ double neg_if(double x, int odd) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(odd & 1) << 63));
+}
+
+// the two removed (or added) spin orbitals of a candidate: `cnt` lane orbitals l0, l1 first, then
+// the candidate's active orbitals from its code (bit positions b0, b1); returned sorted
+__device__ __forceinline__ void merge_pair(const SysDev& S, int cnt, int l0, int l1, unsigned b0, unsigned b1,
+                                           int& x0, int& x1) {
+    const int c0 = act_so(S, (int)(b0 & 63u)), c1 = act_so(S, (int)(b1 & 63u));
+    x0 = cnt >= 1 ? l0 : c0;
+    x1 = cnt == 2 ? l1 : (cnt == 1 ? c0 : c1);
+    if (x0 > x1) {
+        int t = x0;
+        x0 = x1;
+        x1 = t;
+    }
+}
+
+// <m|H|k> for a double candidate: removed = lane's virtual electrons yv + candidate's R',
+// added = lane's core holes xc + candidate's A' (pairing by sorted order, spin conserving)
+template <int W, class C>
+__device__ __forceinline__ double dbl_elem_code(const SysDev& S, const unsigned long long (&m)[2][W], unsigned code,
+                                                int nyv, int yv0, int yv1, int nxc, int xc0, int xc1, C& ctr) {
+    int r1, r2, a1, a2;
+    merge_pair(S, nyv, yv0, yv1, code & 127u, (code >> 7) & 127u, r1, r2);
+    merge_pair(S, nxc, xc0, xc1, (code >> 14) & 127u, (code >> 21) & 127u, a1, a2);
+    const int n = S.n;
+    const int s_r1 = r1 >= n, s_r2 = r2 >= n;
+    const int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - (a1 >= n) * n, pa2 = a2 - (a2 >= n) * n;
+    int c1 = popc_between<W>(m[s_r1], min(pr1, pa1), max(pr1, pa1));
+    int c2;
+    if (s_r2 == s_r1) {
+        unsigned long long t[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) t[w] = m[s_r1][w];
+        flip<W>(t, pr1);
+        flip<W>(t, pa1);
+        c2 = popc_between<W>(t, min(pr2, pa2), max(pr2, pa2));
+    } else {
+        c2 = popc_between<W>(m[s_r2], min(pr2, pa2), max(pr2, pa2));
+    }
+    double v = __ldg(S.eri4 + eri_idx(S, pa1, pr1, pa2, pr2));
+    ctr.g();
+    if (s_r1 == s_r2) {
+        v -= __ldg(S.eri4 + eri_idx(S, pa1, pr2, pa2, pr1));
+        ctr.g();
+    }
+    return neg_if(v, c1 + c2);
+}
+
+// sum over double candidates e0, e0 + stride, ... < e1 of phi_e <m|H|k_e> (list order)
+template <int W, class C>
+__device__ __forceinline__ double cand_sum(const SysDev& S, const unsigned long long (&m)[2][W], const double* cphi,
+                                           const unsigned* ccode, int e0, int e1, int stride, int nyv, int yv0, int yv1,
+                                           int nxc, int xc0, int xc1, C& ctr) {
+    double p0 = 0.0;
+    for (int e = e0; e < e1; e += stride)
+        p0 = fma(cphi[e], dbl_elem_code<W>(S, m, ccode[e], nyv, yv0, yv1, nxc, xc0, xc1, ctr), p0);
+    return p0;
+}
+
+// <m|H|k> for a single candidate x -> y (x: lane's virtual electron or R', y: lane's hole or A')
+template <int W, class C>
+__device__ __forceinline__ double sgl_elem_code(const SysDev& S, const unsigned long long (&m)[2][W], unsigned code,
+                                                int nyv, int yv0, int nxc, int xc0, C& ctr) {
+    const int x = nyv ? yv0 : act_so(S, (int)(code & 127u));
+    const int y = nxc ? xc0 : act_so(S, (int)((code >> 14) & 127u));
+    return single_elem<W>(S, m, x, y, ctr);
+}
+
+// the cnt (1 or 2) items made of k1 "first" items (f0, f1) and then (s0, s1), sorted when cnt = 2
+__device__ __forceinline__ void join_sorted(int cnt, int k1, int f0, int f1, int s0, int s1, int& x0, int& x1) {
+    x0 = k1 >= 1 ? f0 : s0;
+    x1 = k1 == 2 ? f1 : (k1 == 1 ? s0 : s1);
+    if (cnt == 2 && x0 > x1) {
+        int t = x0;
+        x0 = x1;
+        x1 = t;
+    }
+}
+
+// neighbour (ic, iv) of a group: core holes xc, virtual electrons yv, removed / added pairs and m
+template <int W>
+__device__ __forceinline__ void group_neighbour(const SysDev& S, const unsigned long long (&n)[2][W], int nc, int nv,
+                                                int voff, int c, int sc, int v, int sv, int ic, int iv, int ka,
+                                                int xa0, int xa1, int kb, int ya0, int ya1, int r, int& xc0, int& xc1,
+                                                int& yv0, int& yv1, int& rm0, int& rm1, int& ad0, int& ad1,
+                                                unsigned long long (&m)[2][W]) {
+    int t[2] = {0, 0}, u[2] = {0, 0};
+    shape_decode(S, nc, c, sc, 0, ic, t);
+    shape_decode(S, nv, v, sv, voff, iv, u);
+    xc0 = t[0];
+    xc1 = t[1];
+    yv0 = u[0];
+    yv1 = u[1];
+    join_sorted(r, ka, xa0, xa1, xc0, xc1, rm0, rm1);
+    join_sorted(r, kb, ya0, ya1, yv0, yv1, ad0, ad1);
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+        for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
+    {
+        int s1 = rm0 >= S.n, s2 = ad0 >= S.n;
+        flip<W>(m[s1], rm0 - s1 * S.n);
+        flip<W>(m[s2], ad0 - s2 * S.n);
+    }
+    if (r == 2) {
+        int s1 = rm1 >= S.n, s2 = ad1 >= S.n;
+        flip<W>(m[s1], rm1 - s1 * S.n);
+        flip<W>(m[s2], ad1 - s2 * S.n);
+    }
+}
+
+template <int W, int MODE, class C>
+__device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, unsigned* ccode,
+                                   const unsigned long long (&n)[2][W], double psin, unsigned step, unsigned wid,
+                                   int lane, unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc,
+                                   mrq_neighbour* nbout, long long max_nb, C& ctr) {
+    build_lists<W>(S, n, sh, 0, 0, lane);          // occupied lists for the diagonal sums
+    const int nc = S.nc, nv = S.nv, voff = S.nc + S.na;
+    const double c0 = __ldg(S.c);
+    const double inv_psin = psin != 0.0 ? 1.0 / psin : 0.0;
+    const double phin = psin / c0;
+    const unsigned ao0 = active_bits<W>(S, n[0]), ao1 = active_bits<W>(S, n[1]);
+    const unsigned amask = (S.na >= 32) ? 0xFFFFFFFFu : ((1u << S.na) - 1u);
+    const unsigned long long AOn = (unsigned long long)ao0 | ((unsigned long long)ao1 << 32);
+    const unsigned long long AEn =
+        (unsigned long long)(~ao0 & amask) | ((unsigned long long)(~ao1 & amask) << 32);
+    const unsigned long long keyn = hash_key(S, ao0, ao1);
+    const int cntO = __popcll(AOn), cntE = __popcll(AEn);
+    const unsigned lt = (1u << lane) - 1u;
+    LaneAcc<W> acc;
+    lane_acc_init<W>(acc, n);
+    int nbase = 0;     // running neighbour index (debug records)
+
+    // (a) neighbours inside the CAS: active singles and doubles of n
+    for (int r = 1; r <= 2; r++) {
+        const int nY = nsub(cntE, r), tot = nsub(cntO, r) * nY;
+        for (int base = 0; base < tot; base += 32) {
+            const int t = base + lane;
+            bool valid = t < tot;
+            unsigned long long Xb = 0, Yb = 0;
+            if (valid) {
+                const int ix = t / nY;
+                Xb = subset_bits(AOn, cntO, r, ix);
+                Yb = subset_bits(AEn, cntE, r, t - ix * nY);
+                valid = __popcll(Xb & 0xFFFFFFFFull) == __popcll(Yb & 0xFFFFFFFFull);
+            }
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                int rem[2], add[2];
+                act_list(S, Xb, rem);
+                act_list(S, Yb, add);
+                unsigned long long m[2][W];
+#pragma unroll
+                for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+                    for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
+                apply_exc<W>(m, S, rem, add, r);
+                const double hnm = r == 1 ? single_elem<W>(S, n, rem[0], add[0], ctr)
+                                          : double_elem<W>(S, n, rem[0], rem[1], add[0], add[1], ctr);
+                const unsigned long long km = (AOn & ~Xb) | Yb;
+                ctr.cand();
+                const double om = hash_lookup(S, hash_key(S, (unsigned)km, (unsigned)(km >> 32)), ctr);
+                const unsigned exc = r == 1 ? ((unsigned)rem[0] | ((unsigned)rem[0] << 8) | ((unsigned)add[0] << 16) |
+                                               ((unsigned)add[0] << 24))
+                                            : ((unsigned)rem[0] | ((unsigned)rem[1] << 8) | ((unsigned)add[0] << 16) |
+                                               ((unsigned)add[1] << 24));
+                const long long ri = nbase + __popc(vm & lt);
+                lane_post<W, MODE>(S, acc, m, hnm, 0.0, false, om, c0 * om, inv_psin, exc, step, wid,
+                                   (MODE == MODE_DEBUG && nbout != nullptr && ri < max_nb) ? nbout + ri : nullptr);
+            }
+            nbase += __popc(vm);
+        }
+    }
+
+    // (b) neighbours in the FOIS, group by group
+    for (int ka = 0; ka <= 2; ka++) {
+        for (int kb = 0; kb <= 2; kb++) {
+            if (ka == 2 && kb == 2) continue;                   // no room left for core / virtual moves
+            const int nXa = nsub(cntO, ka), nYa = nsub(cntE, kb);
+            for (int xa = 0; xa < nXa; xa++) {
+                const unsigned long long Xb = subset_bits(AOn, cntO, ka, xa);
+                for (int ya = 0; ya < nYa; ya++) {
+                    const unsigned long long Yb = subset_bits(AEn, cntE, kb, ya);
+                    // alpha balance: alpha(X_c) - alpha(Y_v) = alpha(Y_a) - alpha(X_a)
+                    const int d = __popcll(Yb & 0xFFFFFFFFull) - __popcll(Xb & 0xFFFFFFFFull);
+                    const unsigned long long AOm = (AOn & ~Xb) | Yb, AEm = (AEn & ~Yb) | Xb;
+                    const int cO = __popcll(AOm), cE = __popcll(AEm);
+                    // the group's active electrons removed (xa0, xa1) and holes filled (ya0, ya1)
+                    const int xa0 = Xb ? act_so(S, __ffsll(Xb) - 1) : 0;
+                    const int xa1 = (ka == 2) ? act_so(S, 63 - __clzll(Xb)) : 0;
+                    const int ya0 = Yb ? act_so(S, __ffsll(Yb) - 1) : 0;
+                    const int ya1 = (kb == 2) ? act_so(S, 63 - __clzll(Yb)) : 0;
+                    const int rmin = max(1, max(ka, kb));
+                    for (int r = rmin; r <= 2; r++) {
+                        const int c = r - ka, v = r - kb;
+                        if (c == 0 && v == 0) continue;
+                        for (int sc = 0; sc <= c; sc++) {
+                            const int sv = sc - d;
+                            if (sv < 0 || sv > v) continue;
+                            const int ncc = shape_count(nc, c, sc), nvc = shape_count(nv, v, sv);
+                            const int ni = ncc * nvc;
+                            if (ni == 0) continue;
+                            // ---- the group's candidate list (k = n excluded): singles [0, n1), doubles [n1, count)
+                            int count = 0, n1 = 0;
+                            for (int rr = 1; rr <= 2; rr++) {
+                                if (rr == 2) n1 = count;
+                                if (rr == 1 && (c > 1 || v > 1)) continue;
+                                const int ne = rr - v, nf = rr - c;
+                                if (ne < 0 || nf < 0) continue;
+                                const int nA = nsub(cE, nf), tot = nsub(cO, ne) * nA;
+                                for (int base = 0; base < tot; base += 32) {
+                                    const int t = base + lane;
+                                    bool valid = t < tot;
+                                    unsigned long long Rb = 0, Ab = 0;
+                                    double phi = 0.0;
+                                    if (valid) {
+                                        const int iR = t / nA;
+                                        Rb = subset_bits(AOm, cO, ne, iR);
+                                        Ab = subset_bits(AEm, cE, nf, t - iR * nA);
+                                        valid = sv + __popcll(Rb & 0xFFFFFFFFull) == sc + __popcll(Ab & 0xFFFFFFFFull);
+                                    }
+                                    if (valid) {
+                                        const unsigned long long kact = (AOm & ~Rb) | Ab;
+                                        const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
+                                        ctr.cand();
+                                        if (key == keyn) valid = false;
+                                        else {
+                                            phi = hash_lookup(S, key, ctr);
+                                            valid = phi != 0.0;
+                                        }
+                                    }
+                                    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+                                    if (valid) {
+                                        const int pos = count + __popc(vm & lt);
+                                        if (pos < S.cand_cap) {
+                                            cphi[pos] = phi;
+                                            ccode[pos] = pack_cand(Rb, Ab, rr);
+                                        }
+                                    }
+                                    count += __popc(vm);
+                                }
+                            }
+                            if (count > S.cand_cap) {
+                                if (lane == 0) atomicOr(S.err, MRQ_ERR_CAP);
+                                count = S.cand_cap;
+                                n1 = min(n1, count);
+                            }
+                            __syncwarp();
+                            // ---- the group's neighbours: wide groups one lane per neighbour; narrow
+                            // groups one neighbour at a time with the lanes over its candidates
+                            // lane per neighbour (wide: lanes differ in a core / virtual orbital, so their
+                            // integral gathers are adjacent), or for small groups one neighbour at a time with
+                            // the lanes over its candidates (narrow), 32 neighbours per chunk
+                            const bool wide = ni >= 16;
+                            for (int rd = 0; rd < (ni + 31) / 32; rd++) {
+                                double o_narrow = 0.0;
+                                if (!wide) {
+                                    const int qend = min(ni, rd * 32 + 32);
+                                    for (int q = rd * 32; q < qend; q++) {
+                                        int xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1;
+                                        unsigned long long m[2][W];
+                                        const int ic = q / nvc;
+                                        group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, ic, q - ic * nvc, ka, xa0,
+                                                           xa1, kb, ya0, ya1, r, xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1, m);
+                                        double part = 0.0;
+                                        for (int e = lane; e < n1; e += 32)
+                                            part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
+                                        part += cand_sum<W>(S, m, cphi, ccode, n1 + lane, count, 32, v, yv0, yv1, c, xc0,
+                                                            xc1, ctr);
+                                        const double o = warp_sum(part);
+                                        if (lane == q - rd * 32) o_narrow = o;
+                                    }
+                                }
+                                const int q = rd * 32 + lane;
+                                if (q < ni) {
+                                    int xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1;
+                                    unsigned long long m[2][W];
+                                    const int ic = q / nvc;
+                                    group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, ic, q - ic * nvc, ka, xa0, xa1,
+                                                       kb, ya0, ya1, r, xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1, m);
+                                    const double hnm = r == 1 ? single_elem<W>(S, n, rm0, ad0, ctr)
+                                                              : double_elem<W>(S, n, rm0, rm1, ad0, ad1, ctr);
+                                    double om = hnm * phin;        // the k = n term
+                                    if (wide) {
+                                        double part = 0.0;
+                                        for (int e = 0; e < n1; e++)
+                                            part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
+                                        part += cand_sum<W>(S, m, cphi, ccode, n1, count, 1, v, yv0, yv1, c, xc0, xc1, ctr);
+                                        om += part;
+                                    } else {
+                                        om += o_narrow;
+                                    }
+                                    // label of m: holes xc, particles yv
+                                    const int h0 = xc0 >= S.n ? nc + (xc0 - S.n) : xc0;
+                                    const int h1 = xc1 >= S.n ? nc + (xc1 - S.n) : xc1;
+                                    const int p0 = yv0 >= S.n ? nv + (yv0 - S.n - voff) : yv0 - voff;
+                                    const int p1 = yv1 >= S.n ? nv + (yv1 - S.n - voff) : yv1 - voff;
+                                    const long long lm =
+                                        set_rank(c, h0, h1, 2 * nc) * S.nPs + set_rank(v, p0, p1, 2 * nv);
+                                    ctr.g();
+                                    const double psim = __ldg(S.c + lm) * om;
+                                    const unsigned exc =
+                                        r == 1 ? ((unsigned)rm0 | ((unsigned)rm0 << 8) | ((unsigned)ad0 << 16) |
+                                                  ((unsigned)ad0 << 24))
+                                               : ((unsigned)rm0 | ((unsigned)rm1 << 8) | ((unsigned)ad0 << 16) |
+                                                  ((unsigned)ad1 << 24));
+                                    const long long ri = nbase + q;
+                                    lane_post<W, MODE>(S, acc, m, hnm, 0.0, false, om, psim, inv_psin, exc, step, wid,
+                                                       (MODE == MODE_DEBUG && nbout != nullptr && ri < max_nb)
+                                                           ? nbout + ri
+                                                           : nullptr);
+                                }
+                            }
+                            nbase += ni;
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return finish_local<W, MODE>(S, sh, n, 0, lane, acc, nbase, best, best_psi, best_exc);
+}

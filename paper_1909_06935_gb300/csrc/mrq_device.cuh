@@ -19,6 +19,7 @@
 #define MRQ_ERR_HASH 1
 #define MRQ_ERR_NOMOVE 2
 #define MRQ_ERR_LABEL 4
+#define MRQ_ERR_CAP 64          // a candidate list outgrew its shared-memory capacity
 
 struct HashSlot {
     unsigned long long key;
@@ -32,7 +33,8 @@ struct SysDev {
     int nalpha, nbeta;
     long long nPs, nlab;
     unsigned long long mcore[2], mact[2], mvirt[2];   // orbital masks per word (same for both spins)
-    const double* eri;      // packed
+    const double* eri;      // packed (input layout)
+    const double* eri4;     // half-unpacked: E[P(p,q)][r][s] = (pq|rs), n(n+1)/2 x n x n
     const double* hc;       // n*n: h_pq + sum_i [2(pq|ii) - (pi|iq)] (full core)
     const double* h1;       // n*n
     const double* eps;      // n: generalised-Fock diagonal
@@ -40,6 +42,7 @@ struct SysDev {
     const HashSlot* hash;
     unsigned long long hmask;
     int max_probe;
+    int cand_cap;           // per-warp candidate-list capacity (shared memory) of the CAS path
     const double* c;        // nlab sampling coefficients
     // accumulators (G groups)
     double* accN;
@@ -75,10 +78,30 @@ __device__ __forceinline__ long long pair_idx(int p, int q) {
     return p >= q ? (long long)p * (p + 1) / 2 + q : (long long)q * (q + 1) / 2 + p;
 }
 
+// (pq|rs) from the half-unpacked table, arranged by the 8-fold symmetry so that the largest
+// orbital index comes last.  Lanes of a warp usually differ only in a virtual (largest) index,
+// so their gathers land on consecutive addresses.  n <= 128 keeps the index below 2^31.
 __device__ __forceinline__ double eri_g(const SysDev& S, int p, int q, int r, int s) {
-    long long a = pair_idx(p, q), b = pair_idx(r, s);
-    long long i = a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a;
-    return __ldg(S.eri + i);
+    int m1 = p > q ? p : q, m2 = r > s ? r : s;
+    if (m1 > m2) {
+        int t = p; p = r; r = t;
+        t = q; q = s; s = t;
+    }
+    if (r > s) { int t = r; r = s; s = t; }
+    const unsigned P = p >= q ? (unsigned)(p * (p + 1) / 2 + q) : (unsigned)(q * (q + 1) / 2 + p);
+    return __ldg(S.eri4 + (P * (unsigned)S.n + (unsigned)r) * (unsigned)S.n + (unsigned)s);
+}
+
+// index of (pq|rs) in the half-unpacked table (same arrangement as eri_g)
+__device__ __forceinline__ unsigned eri_idx(const SysDev& S, int p, int q, int r, int s) {
+    int m1 = p > q ? p : q, m2 = r > s ? r : s;
+    if (m1 > m2) {
+        int t = p; p = r; r = t;
+        t = q; q = s; s = t;
+    }
+    if (r > s) { int t = r; r = s; s = t; }
+    const unsigned P = p >= q ? (unsigned)(p * (p + 1) / 2 + q) : (unsigned)(q * (q + 1) / 2 + p);
+    return (P * (unsigned)S.n + (unsigned)r) * (unsigned)S.n + (unsigned)s;
 }
 
 // number of set bits of string s strictly between orbitals lo < hi
@@ -291,8 +314,11 @@ __device__ double hd_single_elem(const SysDev& S, const unsigned long long (&d)[
 // virtuals, so the excitation m -> k removes every virtual electron of m (plus active electrons)
 // and fills every core hole (plus active holes): R = P u R', A = H u A', |R| = |A| <= 2.
 
+// `self_key`/`self_term`: when the walker n is itself a CAS determinant, the candidate k = n
+// needs no lookup: its term is H_nm phi0(n), both already known (pass self_key = ~0 otherwise).
 template <int W, class C = NoCtr>
-__device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W], C& ctr) {
+__device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W], C& ctr,
+                             unsigned long long self_key = MRQ_EMPTY_KEY, double self_term = 0.0) {
     const int n = S.n, nc = S.nc, na = S.na;
     int hs[2], ps[2], hc = 0, pc = 0;
 #pragma unroll
@@ -357,7 +383,12 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                 if (xbit >= 0) kact &= ~(1ull << xbit);
                 if (ybit >= 0) kact |= (1ull << ybit);
                 ctr.cand();
-                double c = hash_lookup(S, hash_key(S, (unsigned)kact, (unsigned)(kact >> 32)), ctr);
+                const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
+                if (key == self_key) {
+                    acc += self_term;
+                    continue;
+                }
+                double c = hash_lookup(S, key, ctr);
                 if (c != 0.0) acc += single_elem<W>(S, m, x, y, ctr) * c;
             }
         }
@@ -422,7 +453,12 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                         unsigned long long abits = (c1 >= 0 ? (1ull << c1) : 0ull) | (c2 >= 0 ? (1ull << c2) : 0ull);
                         unsigned long long kact = (AO & ~rbits) | abits;
                         ctr.cand();
-                        double c = hash_lookup(S, hash_key(S, (unsigned)kact, (unsigned)(kact >> 32)), ctr);
+                        const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
+                        if (key == self_key) {
+                            acc += self_term;
+                            continue;
+                        }
+                        double c = hash_lookup(S, key, ctr);
                         if (c == 0.0) continue;
                         int r1 = R[0] < R[1] ? R[0] : R[1], r2 = R[0] < R[1] ? R[1] : R[0];
                         int a1 = A[0] < A[1] ? A[0] : A[1], a2 = A[0] < A[1] ? A[1] : A[0];
