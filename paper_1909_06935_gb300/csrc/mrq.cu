@@ -31,7 +31,10 @@ struct Walker {
     int group;                    // accumulator group
 };
 
+static_assert(sizeof(SysDev) % sizeof(int) == 0, "SysDev is copied word by word");
+
 struct WarpSh {
+    SysDev sys;                      // the walker's system, read by every lane (kept out of local memory)
     unsigned char ol[2][MRQ_MAXN];   // occupied orbitals per spin, ascending (core|active|virtual)
     unsigned char el[2][MRQ_MAXN];   // empty orbitals per spin
     short os[2][4], es[2][4];        // class starts: [spin][class], [3] = count
@@ -491,7 +494,13 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev*
     warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
     WarpSh& sh = *shp;
     Walker wk = walkers[slot];
-    const SysDev S = systems[wk.sys];
+    {
+        const int* src = reinterpret_cast<const int*>(systems + wk.sys);
+        int* dst = reinterpret_cast<int*>(&sh.sys);
+        for (int k = lane; k < (int)(sizeof(SysDev) / sizeof(int)); k += 32) dst[k] = src[k];
+        __syncwarp();
+    }
+    const SysDev& S = sh.sys;
     unsigned long long n[2][W];
 #pragma unroll
     for (int sg = 0; sg < 2; sg++)
@@ -509,9 +518,12 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev*
         if (ln == 0)
             lo = local_eval_cas<W, MODE_STEP>(S, sh, cphi, ccode, n, psin, wk.step, wk.wid, lane, nxt, npsi, nexc,
                                               nullptr, 0, nc);
-        else
+        else {
+            PHASE_T0();
             lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc, nullptr,
                                           0, nc);
+            PHASE_ADD(6);
+        }
         if (!(lo.S > 0.0) || ln < 0) {
             if (lane == 0) atomicOr(S.err, ln < 0 ? MRQ_ERR_LABEL : MRQ_ERR_NOMOVE);
             break;
@@ -560,7 +572,13 @@ __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, c
     unsigned* ccode;
     warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
     WarpSh& sh = *shp;
-    const SysDev S = *sys;
+    {
+        const int* src = reinterpret_cast<const int*>(sys);
+        int* dst = reinterpret_cast<int*>(&sh.sys);
+        for (int k = lane; k < (int)(sizeof(SysDev) / sizeof(int)); k += 32) dst[k] = src[k];
+        __syncwarp();
+    }
+    const SysDev& S = sh.sys;
     unsigned long long n[2][W];
 #pragma unroll
     for (int w = 0; w < W; w++) {
@@ -699,6 +717,18 @@ __global__ void k_expand_eri(const double* __restrict__ eri, double* __restrict_
         long long Q = r >= s ? (long long)r * (r + 1) / 2 + s : (long long)s * (s + 1) / 2 + r;
         long long i = P >= Q ? P * (P + 1) / 2 + Q : Q * (Q + 1) / 2 + P;
         eri4[t] = eri[i];
+    }
+}
+
+// physicists' tables: T[p][q][r][s] = <pq|rs> = (pr|qs) and, after n^4 entries, <pq||rs>
+__global__ void k_build_tab(const SysDev* __restrict__ sys, double* __restrict__ tab) {
+    const SysDev S = *sys;
+    const long long n = S.n, n4 = n * n * n * n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t % n), r = (int)((t / n) % n), q = (int)((t / (n * n)) % n), p = (int)(t / (n * n * n));
+        const double d = eri_g(S, p, r, q, s), x = eri_g(S, p, s, q, r);
+        tab[t] = d;
+        tab[n4 + t] = d - x;
     }
 }
 
@@ -1135,8 +1165,8 @@ struct mrq_ctx {
     int n = 0, nc = 0, na = 0, nv = 0, W = 1, nalpha = 0, nbeta = 0;
     double e_nuc = 0.0;
     long long neri = 0;
-    double *d_h1 = nullptr, *d_eri = nullptr, *d_eri4 = nullptr, *d_hc = nullptr, *d_eps = nullptr,
-           *d_gamma = nullptr;
+    double *d_h1 = nullptr, *d_eri = nullptr, *d_eri4 = nullptr, *d_tab = nullptr, *d_hc = nullptr,
+           *d_eps = nullptr, *d_gamma = nullptr;
     long long nHs = 0, nPs = 0, nlab = 0;
     // reference
     bool ref = false;
@@ -1221,6 +1251,7 @@ static void free_hamiltonian(mrq_ctx* c) {
     dfree(c->d_h1);
     dfree(c->d_eri);
     dfree(c->d_eri4);
+    dfree(c->d_tab);
     dfree(c->d_hc);
     dfree(c->d_eps);
     dfree(c->d_gamma);
@@ -1355,6 +1386,7 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     CK(cudaMalloc(&ctx->d_h1, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eri, sizeof(double) * ctx->neri));
     CK(cudaMalloc(&ctx->d_eri4, sizeof(double) * npair * n * n));
+    CK(cudaMalloc(&ctx->d_tab, sizeof(double) * 2 * (long long)n * n * n * n));
     CK(cudaMalloc(&ctx->d_hc, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eps, sizeof(double) * n));
     CK(cudaMalloc(&ctx->d_gamma, sizeof(double) * std::max(1, n_act * n_act)));
@@ -1382,6 +1414,7 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     }
     s.eri = ctx->d_eri;
     s.eri4 = ctx->d_eri4;
+    s.tab = ctx->d_tab;
     s.h1 = ctx->d_h1;
     s.hc = ctx->d_hc;
     s.eps = ctx->d_eps;
@@ -1408,6 +1441,8 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     }
     if (int r = push_sys(ctx)) return r;
     k_expand_eri<<<1216, 256, 0, ctx->stream>>>(ctx->d_eri, ctx->d_eri4, n);
+    CK(cudaGetLastError());
+    k_build_tab<<<2432, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->d_tab);
     CK(cudaGetLastError());
     k_core_fock<<<(n * n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hc);
     CK(cudaGetLastError());
@@ -1749,6 +1784,16 @@ int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW
     CK(cudaStreamSynchronize(ctx->stream));
     return 0;
 }
+
+#ifdef MRQ_PHASE_TIMING
+int mrq_phase_times(unsigned long long* out8) {
+    cudaDeviceSynchronize();
+    cudaMemcpyFromSymbol(out8, g_phase, sizeof(unsigned long long) * 8);
+    unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaMemcpyToSymbol(g_phase, z, sizeof z);
+    return 0;
+}
+#endif
 
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
     if (!ctx) return MRQ_INVALID_ARG;

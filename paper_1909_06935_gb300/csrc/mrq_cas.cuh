@@ -13,6 +13,15 @@
 // in lockstep; the k = n term needs no lookup.  Every neighbour and every candidate of the plain
 // enumeration is visited exactly once, so the sums are the same as in local_eval.
 
+#ifdef MRQ_PHASE_TIMING
+__device__ unsigned long long g_phase[8];
+#define PHASE_T0() long long _pt0 = clock64()
+#define PHASE_ADD(k) do { long long _pt1 = clock64(); if ((threadIdx.x & 31) == 0) atomicAdd(&g_phase[k], (unsigned long long)(_pt1 - _pt0)); _pt0 = _pt1; } while (0)
+#else
+#define PHASE_T0()
+#define PHASE_ADD(k)
+#endif
+
 __device__ __forceinline__ int nsub(int cnt, int size) {
     return size == 0 ? 1 : (size == 1 ? cnt : cnt * (cnt - 1) / 2);
 }
@@ -152,6 +161,114 @@ __device__ __forceinline__ double dbl_elem_code(const SysDev& S, const unsigned 
     return neg_if(v, c1 + c2);
 }
 
+// A double candidate of a group as a signed table lookup.  With the added pair A = (A0, A1) and the
+// removed pair R = (R0, R1) of m -> k ordered "candidate's active orbitals first, lane's core /
+// virtual orbitals last", <m|H|k> = sgn (-1)^(piA + piR) <A0 A1||R0 R1>, where <A0 A1||R0 R1> is
+// <pq||rs> (same spin), <pq|rs> (A0, R0 same spin) or -<A0 A1|R1 R0>.  Which orbital sits in which slot,
+// piA, piR and the spin pattern do not depend on the lane (the classes fix the order), and sgn
+// changes between lanes only by (-1)^(sum of the lane's core-hole positions): no occupied orbital lies
+// between a virtual and the active block, while the core orbitals above a hole are all occupied.
+// So the entry stores w = phi0(k) * (sign for the reference lane, its core parity removed) and the
+// table index without the lane part; a lane adds its offset and multiplies by its own core parity.
+template <int W>
+__device__ __forceinline__ void dbl_entry(const SysDev& S, const unsigned long long (&mref)[2][W], int c, int v,
+                                          int xc0, int xc1, int yv0, int yv1, int par_ref, unsigned long long Rb,
+                                          unsigned long long Ab, double phi, double& w, unsigned& bp) {
+    const int n = S.n, ne = 2 - v, nf = 2 - c;
+    int rc[2] = {0, 0}, ac[2] = {0, 0};    // candidate's active orbitals, sorted
+    {
+        unsigned long long x = Rb;
+        if (x) { rc[0] = act_so(S, __ffsll(x) - 1); x &= x - 1; }
+        if (x) rc[1] = act_so(S, __ffsll(x) - 1);
+        x = Ab;
+        if (x) { ac[0] = act_so(S, __ffsll(x) - 1); x &= x - 1; }
+        if (x) ac[1] = act_so(S, __ffsll(x) - 1);
+    }
+    const int A0 = nf >= 1 ? ac[0] : xc0, A1 = nf == 2 ? ac[1] : (nf == 1 ? xc0 : xc1);
+    const int R0 = ne >= 1 ? rc[0] : yv0, R1 = ne == 2 ? rc[1] : (ne == 1 ? yv0 : yv1);
+    const int a1 = min(A0, A1), a2 = max(A0, A1), r1 = min(R0, R1), r2 = max(R0, R1);
+    const int piA = A0 > A1, piR = R0 > R1;
+    // sign of the reference lane's element (pairing r1 -> a1, r2 -> a2, sequential singles on m)
+    const int s_r1 = r1 >= n, s_r2 = r2 >= n;
+    const int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - (a1 >= n) * n, pa2 = a2 - (a2 >= n) * n;
+    int c1 = popc_between<W>(mref[s_r1], min(pr1, pa1), max(pr1, pa1));
+    int c2;
+    if (s_r2 == s_r1) {
+        unsigned long long t[W];
+#pragma unroll
+        for (int w2 = 0; w2 < W; w2++) t[w2] = mref[s_r1][w2];
+        flip<W>(t, pr1);
+        flip<W>(t, pa1);
+        c2 = popc_between<W>(t, min(pr2, pa2), max(pr2, pa2));
+    } else {
+        c2 = popc_between<W>(mref[s_r2], min(pr2, pa2), max(pr2, pa2));
+    }
+    const int sA0 = A0 >= n, sA1 = A1 >= n, sR0 = R0 >= n, sR1 = R1 >= n;
+    const bool same = sA0 == sA1 && sR0 == sR1 && sA0 == sR0;
+    const bool xpat = !same && sA0 != sR0;              // the allowed pairing is (A0,R1)(A1,R0)
+    const unsigned nn = (unsigned)n, n2 = nn * nn, n3 = n2 * nn;
+    const unsigned pA0 = (unsigned)(A0 - sA0 * n), pA1 = (unsigned)(A1 - sA1 * n);
+    const unsigned pR0 = (unsigned)(R0 - sR0 * n), pR1 = (unsigned)(R1 - sR1 * n);
+    unsigned base = same ? n3 * nn : 0u;
+    if (nf >= 1) base += pA0 * n3;
+    if (nf == 2) base += pA1 * n2;
+    if (!xpat) {
+        if (ne >= 1) base += pR0 * nn;
+        if (ne == 2) base += pR1;
+    } else {
+        if (ne == 2) base += pR1 * nn;
+        if (ne >= 1) base += pR0;
+    }
+    const int odd = c1 + c2 + piA + piR + (xpat ? 1 : 0) + par_ref;
+    w = neg_if(phi, odd);
+    bp = base | (xpat ? 0x80000000u : 0u);
+}
+
+// a lane's table offsets for the direct and the swapped removed-pair layouts, and its core parity
+__device__ __forceinline__ void lane_offsets(const SysDev& S, int c, int v, int xc0, int xc1, int yv0, int yv1,
+                                             unsigned& off_d, unsigned& off_x, int& par) {
+    const unsigned nn = (unsigned)S.n, n2 = nn * nn, n3 = n2 * nn;
+    const unsigned p0 = (unsigned)(xc0 % S.n), p1 = (unsigned)(xc1 % S.n);
+    const unsigned v0 = (unsigned)(yv0 % S.n), v1 = (unsigned)(yv1 % S.n);
+    const unsigned core = c == 2 ? p0 * n3 + p1 * n2 : (c == 1 ? p0 * n2 : 0u);
+    off_d = core + (v == 2 ? v0 * nn + v1 : (v == 1 ? v0 : 0u));
+    off_x = core + (v == 2 ? v1 * nn + v0 : (v == 1 ? v0 * nn : 0u));
+    par = (c >= 1 ? (int)p0 : 0) + (c == 2 ? (int)p1 : 0);
+}
+
+// sum over the table-form double candidates e0, e0 + stride, ... < e1 (list order)
+template <class C>
+__device__ __forceinline__ double tab_sum(const SysDev& S, const double* cphi, const unsigned* ccode, int e0, int e1,
+                                          int stride, unsigned off_d, unsigned off_x, C& ctr) {
+#ifndef MRQ_TAB_UNROLL
+#define MRQ_TAB_UNROLL 4
+#endif
+    double p[MRQ_TAB_UNROLL];
+#pragma unroll
+    for (int k = 0; k < MRQ_TAB_UNROLL; k++) p[k] = 0.0;
+    int e = e0;
+    for (; e + (MRQ_TAB_UNROLL - 1) * stride < e1; e += MRQ_TAB_UNROLL * stride) {
+        double x[MRQ_TAB_UNROLL];
+#pragma unroll
+        for (int k = 0; k < MRQ_TAB_UNROLL; k++) {
+            const unsigned bp = ccode[e + k * stride];
+            x[k] = __ldg(S.tab + (bp & 0x7FFFFFFFu) + ((bp & 0x80000000u) ? off_x : off_d));
+        }
+#pragma unroll
+        for (int k = 0; k < MRQ_TAB_UNROLL; k++) p[k] = fma(cphi[e + k * stride], x[k], p[k]);
+        ctr.g(MRQ_TAB_UNROLL);
+    }
+    for (; e < e1; e += stride) {
+        const unsigned bp = ccode[e];
+        p[0] = fma(cphi[e], __ldg(S.tab + (bp & 0x7FFFFFFFu) + ((bp & 0x80000000u) ? off_x : off_d)), p[0]);
+        ctr.g();
+    }
+    double t = p[0];
+#pragma unroll
+    for (int k = 1; k < MRQ_TAB_UNROLL; k++) t += p[k];
+    return t;
+}
+
 // sum over double candidates e0, e0 + stride, ... < e1 of phi_e <m|H|k_e> (list order)
 template <int W, class C>
 __device__ __forceinline__ double cand_sum(const SysDev& S, const unsigned long long (&m)[2][W], const double* cphi,
@@ -236,6 +353,7 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
     LaneAcc<W> acc;
     lane_acc_init<W>(acc, n);
     int nbase = 0;     // running neighbour index (debug records)
+    PHASE_T0();
 
     // (a) neighbours inside the CAS: active singles and doubles of n
     for (int r = 1; r <= 2; r++) {
@@ -278,6 +396,7 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
         }
     }
 
+    PHASE_ADD(0);
     // (b) neighbours in the FOIS, group by group
     for (int ka = 0; ka <= 2; ka++) {
         for (int kb = 0; kb <= 2; kb++) {
@@ -306,7 +425,15 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                             const int ncc = shape_count(nc, c, sc), nvc = shape_count(nv, v, sv);
                             const int ni = ncc * nvc;
                             if (ni == 0) continue;
-                            // ---- the group's candidate list (k = n excluded): singles [0, n1), doubles [n1, count)
+                            PHASE_ADD(1);
+                            // reference lane (the group's first neighbour) for the candidates' signs
+                            int rxc0, rxc1, ryv0, ryv1, rrm0, rrm1, rad0, rad1;
+                            unsigned long long mref[2][W];
+                            group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, 0, 0, ka, xa0, xa1, kb, ya0, ya1, r,
+                                               rxc0, rxc1, ryv0, ryv1, rrm0, rrm1, rad0, rad1, mref);
+                            const int par_ref = (c >= 1 ? rxc0 % S.n : 0) + (c == 2 ? rxc1 % S.n : 0);
+                            // ---- the group's candidate list (k = n excluded): singles [0, n1) as codes,
+                            // doubles [n1, count) as (signed weight, table base)
                             int count = 0, n1 = 0;
                             for (int rr = 1; rr <= 2; rr++) {
                                 if (rr == 2) n1 = count;
@@ -339,8 +466,17 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                     if (valid) {
                                         const int pos = count + __popc(vm & lt);
                                         if (pos < S.cand_cap) {
-                                            cphi[pos] = phi;
-                                            ccode[pos] = pack_cand(Rb, Ab, rr);
+                                            if (rr == 1) {
+                                                cphi[pos] = phi;
+                                                ccode[pos] = pack_cand(Rb, Ab, rr);
+                                            } else {
+                                                double w;
+                                                unsigned bp;
+                                                dbl_entry<W>(S, mref, c, v, rxc0, rxc1, ryv0, ryv1, par_ref, Rb, Ab,
+                                                             phi, w, bp);
+                                                cphi[pos] = w;
+                                                ccode[pos] = bp;
+                                            }
                                         }
                                     }
                                     count += __popc(vm);
@@ -352,6 +488,7 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                 n1 = min(n1, count);
                             }
                             __syncwarp();
+                            PHASE_ADD(2);
                             // ---- the group's neighbours: wide groups one lane per neighbour; narrow
                             // groups one neighbour at a time with the lanes over its candidates
                             // lane per neighbour (wide: lanes differ in a core / virtual orbital, so their
@@ -371,8 +508,10 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                         double part = 0.0;
                                         for (int e = lane; e < n1; e += 32)
                                             part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
-                                        part += cand_sum<W>(S, m, cphi, ccode, n1 + lane, count, 32, v, yv0, yv1, c, xc0,
-                                                            xc1, ctr);
+                                        unsigned offd, offx;
+                                        int par;
+                                        lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
+                                        part += neg_if(tab_sum(S, cphi, ccode, n1 + lane, count, 32, offd, offx, ctr), par);
                                         const double o = warp_sum(part);
                                         if (lane == q - rd * 32) o_narrow = o;
                                     }
@@ -391,7 +530,10 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                         double part = 0.0;
                                         for (int e = 0; e < n1; e++)
                                             part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
-                                        part += cand_sum<W>(S, m, cphi, ccode, n1, count, 1, v, yv0, yv1, c, xc0, xc1, ctr);
+                                        unsigned offd, offx;
+                                        int par;
+                                        lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
+                                        part += neg_if(tab_sum(S, cphi, ccode, n1, count, 1, offd, offx, ctr), par);
                                         om += part;
                                     } else {
                                         om += o_narrow;
@@ -419,11 +561,15 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                             }
                             nbase += ni;
                             __syncwarp();
+                            if (wide) PHASE_ADD(3); else PHASE_ADD(4);
                         }
                     }
                 }
             }
         }
     }
-    return finish_local<W, MODE>(S, sh, n, 0, lane, acc, nbase, best, best_psi, best_exc);
+    PHASE_ADD(1);
+    LocalOut lo = finish_local<W, MODE>(S, sh, n, 0, lane, acc, nbase, best, best_psi, best_exc);
+    PHASE_ADD(5);
+    return lo;
 }
