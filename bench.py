@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "cas10_56o"
 METRIC = "walker-steps/s"
+# FP64 FMA pipe of GB300: 2 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# random 8-byte loads from an L2-resident table, measured on this machine's GB300 (loads/s)
+L2_GATHER_PEAK = 3.14e11
 
 
 def parse():
@@ -225,21 +229,30 @@ def run_ours(args):
     units = nw * inner * args.steps
     value = world * units / (ms / 1e3)
 
-    # algorithmic accesses per walker-step from the counting kernel on walker snapshots
+    # algorithmic work per walker-step, counted exactly by the debug kernel on walker snapshots taken
+    # before and after the timed region: every reach-back term H_mk phi0(k) is one FP64 FMA (2 flops),
+    # every neighbour adds <n|H|m>, the ratio, the rate and three sums (8 flops)
     locs = [ctx.debug_local(snap)[0] for snap in (snap0, snap1)]
-    acc_per_step = float(np.mean([np.mean(32.0 * (l["n_gathers"] + l["n_probes"])) for l in locs]))
-    cand_per_step = float(np.mean([np.mean(l["n_candidates"]) for l in locs]))
-    nb_per_step = float(np.mean([np.mean(l["n_neighbours"]) for l in locs]))
-
+    terms = float(np.mean([np.mean(l["n_terms"]) for l in locs]))
+    nbrs = float(np.mean([np.mean(l["n_neighbours"]) for l in locs]))
+    gathers = float(np.mean([np.mean(l["n_gathers"] + l["n_probes"]) for l in locs]))
+    flops_per_step = 2.0 * terms + 8.0 * nbrs
     launch_s = walk_s / max(walk_launches, 1)
-    bytes_per_launch = acc_per_step * nw * inner
+    units_per_launch = nw * inner
+    fp64_peak = FP64_PEAK_TFLOPS
+    achieved = flops_per_step * units_per_launch / launch_s / 1e12
     peaks, peak_kind = load_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_per_launch / launch_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "k_walk", "peak_source": f"{peak_kind} hbm_gbs",
-            "algorithmic_bytes_per_walker_step": acc_per_step, "launch_seconds": launch_s,
-            "launches_timed": int(walk_launches)}
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_walk",
+            "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (probe on this pool: 1.254 TFLOP/s)",
+            "flops_per_walker_step": flops_per_step, "terms_per_walker_step": terms,
+            "launch_seconds": launch_s, "launches_timed": int(walk_launches),
+            "gathers_per_walker_step": gathers,
+            "l2_gather_rate_per_s": gathers * units_per_launch / launch_s,
+            "l2_gather_peak_per_s": L2_GATHER_PEAK, "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+            "hbm_peak_source": peak_kind}
+    cand_per_step = float(np.mean([np.mean(l["n_candidates"]) for l in locs]))
+    nb_per_step = nbrs
 
     # end to end through the public API with host buffers (inputs copied in every step)
     e2e = None

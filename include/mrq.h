@@ -104,6 +104,7 @@ typedef struct {
     int64_t n_candidates; /* reach-back candidates tried (hash lookups of neighbours and of their CAS images) */
     int64_t n_probes;     /* hash slots read (16 B each) */
     int64_t n_gathers;    /* 8 B random reads of integrals and per-orbital / per-label tables */
+    int64_t n_terms;      /* products <m|H|k> phi0(k) summed into the overlaps O(m) (one FP64 FMA each) */
 } mrq_local;
 
 /* Per-neighbour record of mrq_debug_local. */

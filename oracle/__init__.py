@@ -69,6 +69,8 @@ def _load():
             lib.oracle_brute.restype = C.c_int
             lib.oracle_brute.argtypes = [P, P, P, P]
             lib.oracle_philox.argtypes = [P, P, P]
+            lib.oracle_walk_one.restype = C.c_int
+            lib.oracle_walk_one.argtypes = [P, C.c_uint32, C.c_int64, C.c_uint64, P]
             _lib = lib
     return _lib
 
@@ -162,7 +164,7 @@ class Oracle:
         else:
             k = self._lib.oracle_local(self._h, _ptr(self._det(d)), _ptr(out), 0, None, None, None)
         r = dict(S=out[0], EL=out[1], num=out[2], Hnn=out[3], HDnn=out[4], psi=out[5], label=int(out[6]),
-                 type=int(out[7]), nnb=int(out[8]))
+                 type=int(out[7]), nnb=int(out[8]), terms=int(out[9]))
         if max_nb:
             k = min(k, max_nb)
             r.update(dets=nd[:k], H=nv[:k, 0], HD=nv[:k, 1], O=nv[:k, 2], psi_m=nv[:k, 3], Gamma=nv[:k, 4],
@@ -174,6 +176,14 @@ class Oracle:
         out = np.zeros(4)
         exc = self._lib.oracle_move(self._h, _ptr(self._det(d)), seed, step, walker, _ptr(nxt), _ptr(out))
         return nxt, int(exc), dict(S=out[0], EL=out[1], num=out[2], psi_next=out[3])
+
+    def walk_one(self, walker: int, n_steps: int, seed: int):
+        """Trajectory (n_steps x 2W) of one walker from the start determinant."""
+        traj = np.zeros((n_steps, 2 * self.W), np.uint64)
+        rc = self._lib.oracle_walk_one(self._h, walker, n_steps, seed, _ptr(traj))
+        if rc:
+            raise RuntimeError(f"oracle_walk_one failed with status {rc}")
+        return traj
 
     # ---- the walk
     def sample(self, n_walkers: int, n_steps: int, burn_in: int, seed: int, n_groups: int,

@@ -258,7 +258,7 @@ static double hd_elem(const osys *S, const det_t *nd, const det_t *md) {
 /* O(m) = <m|H|phi0> for m outside the CAS: the determinants k of phi0 reachable from m must
  * have a full core and empty virtuals, so the excitation m->k removes every virtual electron
  * of m plus active electrons, and fills every core hole plus active holes (Sec. II D). */
-static double overlap_foism(const osys *S, const det_t *m) {
+static double overlap_foism(const osys *S, const det_t *m, int64_t *terms) {
     int n = S->n, rp[2 * MAXN], ap[2 * MAXN], nrp = 0, nap = 0, h = 0, p = 0;
     for (int so = 0; so < 2 * n; so++) {
         int cl = orb_class(S, so % n), o = occ(m, so, n);
@@ -278,7 +278,7 @@ static double overlap_foism(const osys *S, const det_t *m) {
                 if (h == 1 && orb_class(S, a % n) != 0) continue;
                 det_t k = *m; clrb(&k, r, n); setb(&k, a, n);
                 double c = phi0(S, &k);
-                if (c != 0.0) acc += h_elem(S, m, &k) * c;
+                if (c != 0.0) { acc += h_elem(S, m, &k) * c; if (terms) (*terms)++; }
             }
     /* doubles */
     for (int x1 = 0; x1 < nrp; x1++)
@@ -295,22 +295,23 @@ static double overlap_foism(const osys *S, const det_t *m) {
                     det_t k = *m;
                     clrb(&k, rp[x1], n); clrb(&k, rp[x2], n); setb(&k, ap[y1], n); setb(&k, ap[y2], n);
                     double c = phi0(S, &k);
-                    if (c != 0.0) acc += h_elem(S, m, &k) * c;
+                    if (c != 0.0) { acc += h_elem(S, m, &k) * c; if (terms) (*terms)++; }
                 }
         }
     return acc;
 }
 
 /* <m|psi_s> = c_0 phi0(m) in the CAS, c_{l_m} O(m) in the FOIS, 0 outside (Eq. 6-7, 17) */
-static double psi_s(const osys *S, const det_t *m, double *o_out) {
+static double psi_s_t(const osys *S, const det_t *m, double *o_out, int64_t *terms) {
     int h, p;
     int64_t l = det_label(S, m, &h, &p);
     if (l < 0) { if (o_out) *o_out = 0.0; return 0.0; }
     if (l == 0) { double v = phi0(S, m); if (o_out) *o_out = v; return S->c[0] * v; }
-    double o = overlap_foism(S, m);
+    double o = overlap_foism(S, m, terms);
     if (o_out) *o_out = o;
     return S->c[l] * o;
 }
+static double psi_s(const osys *S, const det_t *m, double *o_out) { return psi_s_t(S, m, o_out, NULL); }
 
 /* ------------------------------------------------------------------ Philox4x32-10
  * Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11). */
@@ -351,6 +352,7 @@ static double race_clock(uint64_t seed, uint32_t exc, uint32_t step, uint32_t wa
 
 typedef struct {
     double S, EL, num, Hnn, HDnn, psi_n;
+    int64_t terms;      /* products H_mk phi0(k) summed into the neighbours' overlaps */
     int64_t label;
     int type;
     int64_t nnb;
@@ -390,7 +392,7 @@ static void local_eval(const osys *S, const det_t *d, int do_move, uint64_t seed
                         if (kind == 2) { clrb(&m, r2, n); setb(&m, a2, n); }
                         int64_t lm = det_label(S, &m, NULL, NULL);
                         if (lm < 0) continue;
-                        double o, ps = psi_s(S, &m, &o);
+                        double o, ps = psi_s_t(S, &m, &o, &L->terms);
                         double hnm = h_elem(S, d, &m);
                         double hd = (L->label > 0 && lm == L->label) ? hd_elem(S, d, &m) : 0.0;
                         double ratio = (L->psi_n != 0.0) ? ps / L->psi_n : 0.0;
@@ -593,7 +595,7 @@ double oracle_psi(void *h, const uint64_t *x, double *o) {
 }
 
 /* local quantities of one determinant.
- * out[0..9] = S, E_L, num, H_nn, HD_nn, psi_n, label, type, n_neighbours, 0
+ * out[0..9] = S, E_L, num, H_nn, HD_nn, psi_n, label, type, n_neighbours, reach-back terms
  * per neighbour k: dets[k*2W..], vals[k*5..] = H_nm, HD_nm, O(m)|phi0(m), psi_s(m), Gamma, exc[k] */
 int64_t oracle_local(void *h, const uint64_t *x, double *out, int64_t max_nb, uint64_t *nb_dets,
                      double *nb_vals, uint32_t *nb_exc) {
@@ -602,7 +604,7 @@ int64_t oracle_local(void *h, const uint64_t *x, double *out, int64_t max_nb, ui
     local_t L;
     local_eval(S, &d, 0, 0, 0, 0, &L, max_nb, nb_dets, nb_vals, nb_exc);
     out[0] = L.S; out[1] = L.EL; out[2] = L.num; out[3] = L.Hnn; out[4] = L.HDnn; out[5] = L.psi_n;
-    out[6] = (double)L.label; out[7] = (double)L.type; out[8] = (double)L.nnb; out[9] = 0.0;
+    out[6] = (double)L.label; out[7] = (double)L.type; out[8] = (double)L.nnb; out[9] = (double)L.terms;
     return L.nnb;
 }
 
@@ -672,6 +674,21 @@ int oracle_sample(void *h, int64_t nwalk, int64_t nsteps, int64_t burn, uint64_t
         }
     free(rl); free(rt); free(rw); free(rn); free(re);
     return bad ? -4 : 0;
+}
+
+/* One walker (id `walker`) from the start determinant for nsteps steps; traj receives the
+ * determinant after every step (nsteps x 2W words).  Returns 0, or -4 when it has no move. */
+int oracle_walk_one(void *h, uint32_t walker, int64_t nsteps, uint64_t seed, uint64_t *traj) {
+    osys *S = (osys *)h;
+    det_t d = S->start_det;
+    for (int64_t s = 0; s < nsteps; s++) {
+        local_t L;
+        local_eval(S, &d, 1, seed, (uint32_t)s, walker, &L, 0, NULL, NULL, NULL);
+        if (!(L.S > 0.0)) return -4;
+        d = L.next;
+        det_to_words(S, &d, traj + s * 2 * S->W);
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ brute force (tiny systems)

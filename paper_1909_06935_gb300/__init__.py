@@ -51,7 +51,7 @@ class Local(C.Structure):
     _fields_ = [("S", C.c_double), ("e_local", C.c_double), ("num", C.c_double), ("h_nn", C.c_double),
                 ("hd_nn", C.c_double), ("psi", C.c_double), ("label", C.c_int64), ("type", C.c_int64),
                 ("n_neighbours", C.c_int64), ("n_candidates", C.c_int64), ("n_probes", C.c_int64),
-                ("n_gathers", C.c_int64)]
+                ("n_gathers", C.c_int64), ("n_terms", C.c_int64)]
 
 
 class Neighbour(C.Structure):
@@ -64,7 +64,7 @@ _NB_DTYPE = np.dtype([("det", np.uint64, 4), ("h", np.float64), ("hd", np.float6
 _LOCAL_DTYPE = np.dtype([("S", np.float64), ("e_local", np.float64), ("num", np.float64), ("h_nn", np.float64),
                          ("hd_nn", np.float64), ("psi", np.float64), ("label", np.int64), ("type", np.int64),
                          ("n_neighbours", np.int64), ("n_candidates", np.int64), ("n_probes", np.int64),
-                         ("n_gathers", np.int64)])
+                         ("n_gathers", np.int64), ("n_terms", np.int64)])
 assert _NB_DTYPE.itemsize == C.sizeof(Neighbour) and _LOCAL_DTYPE.itemsize == C.sizeof(Local)
 
 

@@ -480,14 +480,19 @@ __device__ __forceinline__ void warp_smem(unsigned char* base, int cap, WarpSh*&
     ccode = reinterpret_cast<unsigned*>(cphi + cap);
 }
 
+// One warp per walker slot.  Slot s advances walker order[s] (or s when order is null) by nsteps;
+// ordering the slots by determinant puts walkers that sit on the same determinant into
+// neighbouring warps, which then share cache lines (the results do not depend on the order).
 template <int W>
 __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev* __restrict__ systems,
                                                                    Walker* __restrict__ walkers, long long nslots,
-                                                                   int nsteps, int cap) {
+                                                                   int nsteps, int cap,
+                                                                   const unsigned* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const long long slot = (long long)blockIdx.x * 4 + wi;
-    if (slot >= nslots) return;
+    const long long s0 = (long long)blockIdx.x * 4 + wi;
+    if (s0 >= nslots) return;
+    const long long slot = order ? (long long)order[s0] : s0;
     WarpSh* shp;
     double* cphi;
     unsigned* ccode;
@@ -557,6 +562,68 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev*
     }
 }
 
+// sort key of a walker slot: system, label, then the active occupation (truncated), and the slot
+template <int W>
+__global__ void k_walker_keys(const SysDev* __restrict__ systems, const Walker* __restrict__ walkers,
+                              long long nslots, long long npad, unsigned long long* __restrict__ keys,
+                              unsigned* __restrict__ idx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i >= nslots) {
+        keys[i] = ~0ull;
+        idx[i] = 0xFFFFFFFFu;
+        return;
+    }
+    const Walker wk = walkers[i];
+    const SysDev& S = systems[wk.sys];
+    unsigned long long d[2][W];
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+        for (int w = 0; w < W; w++) d[sg][w] = wk.d[sg][w];
+    int h, p;
+    const long long l = det_label<W>(S, d, h, p);
+    const unsigned long long act = hash_key(S, active_bits<W>(S, d[0]), active_bits<W>(S, d[1]));
+    keys[i] = ((unsigned long long)(wk.sys & 0xFFFF) << 48) | ((unsigned long long)(l & 0xFFFFFF) << 24) |
+              (act & 0xFFFFFFull);
+    idx[i] = (unsigned)i;
+}
+
+// one-block bitonic sort of (key, index) pairs in shared memory, npad a power of two <= MRQ_SORT_MAX
+#define MRQ_SORT_MAX 8192
+__global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict__ keys, unsigned* __restrict__ idx,
+                                                  int npad) {
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(sort_smem);
+    unsigned* si = reinterpret_cast<unsigned*>(sk + npad);
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+        sk[i] = keys[i];
+        si[i] = idx[i];
+    }
+    __syncthreads();
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = sk[i], b = sk[ixj];
+                    const bool swap = up ? (a > b || (a == b && si[i] > si[ixj])) : (a < b || (a == b && si[i] < si[ixj]));
+                    if (swap) {
+                        sk[i] = b;
+                        sk[ixj] = a;
+                        const unsigned t = si[i];
+                        si[i] = si[ixj];
+                        si[ixj] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) idx[i] = si[i];
+}
+
 // local quantities of arbitrary determinants (parity); CAS determinants take the same grouped
 // path as the walk
 template <int W>
@@ -611,14 +678,16 @@ __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, c
                                            ctr);
     else
         lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb, ctr);
-    unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands;
+    unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands, ct = ctr.terms;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         cg += __shfl_xor_sync(0xffffffffu, cg, o);
         cp += __shfl_xor_sync(0xffffffffu, cp, o);
         cc += __shfl_xor_sync(0xffffffffu, cc, o);
+        ct += __shfl_xor_sync(0xffffffffu, ct, o);
     }
     if (lane == 0) {
+        r.n_terms = (long long)ct;
         r.n_gathers = (long long)cg;
         r.n_probes = (long long)cp;
         r.n_candidates = (long long)cc;
@@ -1192,6 +1261,9 @@ struct mrq_ctx {
     long long acc_lab = 0;
     int acc_G = 0;
     int* d_err = nullptr;
+    unsigned long long* d_sort_keys = nullptr;   // walker-slot ordering by determinant
+    unsigned* d_sort_idx = nullptr;
+    long long sort_cap = 0;
     double* d_partial = nullptr;
     long long partial_cap = 0;
     mrq_result* d_res = nullptr;
@@ -1287,6 +1359,43 @@ static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
     return 0;
 }
 
+// walk launch: order the slots by determinant (when the walker count allows a one-block sort),
+// then one warp per slot
+static int launch_walk(mrq_ctx* ctx, int W, const SysDev* d_systems, Walker* d_walkers, long long nslots, int nsteps,
+                       int cap) {
+    const size_t smem = 4 * warp_smem_bytes(cap);
+    const unsigned* order = nullptr;
+    if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
+        long long npad = 1;
+        while (npad < nslots) npad <<= 1;
+        if (npad > ctx->sort_cap) {
+            dfree(ctx->d_sort_keys);
+            dfree(ctx->d_sort_idx);
+            CK(cudaMalloc(&ctx->d_sort_keys, sizeof(unsigned long long) * npad));
+            CK(cudaMalloc(&ctx->d_sort_idx, sizeof(unsigned) * npad));
+            ctx->sort_cap = npad;
+        }
+        const unsigned nb = (unsigned)((npad + 255) / 256);
+        if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(d_systems, d_walkers, nslots, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+        else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(d_systems, d_walkers, nslots, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+        const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
+        CK(cudaFuncSetAttribute(k_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+        k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
+        CK(cudaGetLastError());
+        order = ctx->d_sort_idx;
+    }
+    const unsigned blocks = (unsigned)((nslots + 3) / 4);
+    if (W == 1) {
+        CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(d_systems, d_walkers, nslots, nsteps, cap, order);
+    } else {
+        CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(d_systems, d_walkers, nslots, nsteps, cap, order);
+    }
+    CK(cudaGetLastError());
+    return 0;
+}
+
 extern "C" {
 
 int mrq_create(mrq_ctx** out, int device) {
@@ -1329,6 +1438,8 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_err);
     dfree(ctx->d_sys);
     dfree(ctx->d_res);
+    dfree(ctx->d_sort_keys);
+    dfree(ctx->d_sort_idx);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1676,7 +1787,6 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     if (!ctx->ref || !ctx->d_walk || ctx->nwalk == 0) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
     if (n_steps <= 0) return 0;
     CK(cudaSetDevice(ctx->device));
-    const unsigned blocks = (unsigned)((ctx->nwalk + 3) / 4);
     const size_t k = (size_t)ctx->launches * 2;
     while (ctx->evs.size() < k + 2) {
         cudaEvent_t e;
@@ -1684,15 +1794,8 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
         ctx->evs.push_back(e);
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
-    const int cap = ctx->hsys.cand_cap;
-    const size_t smem = 4 * warp_smem_bytes(cap);
-    if (ctx->W == 1) {
-        CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, cap);
-    } else {
-        CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, cap);
-    }
+    if (int r = launch_walk(ctx, ctx->W, ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, ctx->hsys.cand_cap))
+        return r;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
     ctx->launches++;

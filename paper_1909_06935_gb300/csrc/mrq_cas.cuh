@@ -538,6 +538,7 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                     } else {
                                         om += o_narrow;
                                     }
+                                    ctr.term(count + 1);
                                     // label of m: holes xc, particles yv
                                     const int h0 = xc0 >= S.n ? nc + (xc0 - S.n) : xc0;
                                     const int h1 = xc1 >= S.n ? nc + (xc1 - S.n) : xc1;

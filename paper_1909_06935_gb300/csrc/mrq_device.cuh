@@ -65,12 +65,14 @@ struct NoCtr {
     __device__ __forceinline__ void g(int = 1) {}
     __device__ __forceinline__ void pr(int = 1) {}
     __device__ __forceinline__ void cand() {}
+    __device__ __forceinline__ void term(int = 1) {}
 };
 struct Ctr {
-    unsigned long long gathers = 0, probes = 0, cands = 0;
+    unsigned long long gathers = 0, probes = 0, cands = 0, terms = 0;
     __device__ __forceinline__ void g(int k = 1) { gathers += k; }
     __device__ __forceinline__ void pr(int k = 1) { probes += k; }
     __device__ __forceinline__ void cand() { cands++; }
+    __device__ __forceinline__ void term(int k = 1) { terms += k; }   // H_mk phi0(k) products summed
 };
 
 // ------------------------------------------------------------------ small helpers
@@ -387,10 +389,14 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                 const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
                 if (key == self_key) {
                     acc += self_term;
+                    ctr.term();
                     continue;
                 }
                 double c = hash_lookup(S, key, ctr);
-                if (c != 0.0) acc += single_elem<W>(S, m, x, y, ctr) * c;
+                if (c != 0.0) {
+                    acc += single_elem<W>(S, m, x, y, ctr) * c;
+                    ctr.term();
+                }
             }
         }
     }
@@ -457,10 +463,12 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                         const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
                         if (key == self_key) {
                             acc += self_term;
+                            ctr.term();
                             continue;
                         }
                         double c = hash_lookup(S, key, ctr);
                         if (c == 0.0) continue;
+                        ctr.term();
                         int r1 = R[0] < R[1] ? R[0] : R[1], r2 = R[0] < R[1] ? R[1] : R[0];
                         int a1 = A[0] < A[1] ? A[0] : A[1], a2 = A[0] < A[1] ? A[1] : A[0];
                         acc += double_elem<W>(S, m, r1, r2, a1, a2, ctr) * c;

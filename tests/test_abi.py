@@ -30,9 +30,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts_match_header_sizes():
-    # mrq_neighbour: 4 words + 5 doubles + 2 uint32 = 80 bytes; mrq_local: 6 doubles + 6 int64 = 96
+    # mrq_neighbour: 4 words + 5 doubles + 2 uint32 = 80 bytes; mrq_local: 6 doubles + 7 int64 = 104
     assert ctypes.sizeof(P.Neighbour) == 80
-    assert ctypes.sizeof(P.Local) == 96
+    assert ctypes.sizeof(P.Local) == 104
     assert ctypes.sizeof(P.SampleParams) == 56
 
 

@@ -36,6 +36,7 @@ def compare_local(ctx, orc, dets, W):
         assert loc["label"][i] == r["label"]
         assert loc["type"][i] == r["type"]
         assert loc["n_neighbours"][i] == r["nnb"]
+        assert loc["n_terms"][i] == r["terms"]            # the roofline's algorithmic count
         for key_g, key_o in (("S", "S"), ("e_local", "EL"), ("num", "num"), ("h_nn", "Hnn"), ("hd_nn", "HDnn"),
                              ("psi", "psi")):
             assert close(loc[key_g][i], r[key_o]), (i, key_g, loc[key_g][i], r[key_o])
@@ -182,3 +183,28 @@ def test_errors_are_reported():
     assert e.value.code == -1
     with pytest.raises(P.MRQError):
         ctx.walkers_advance(3)
+
+
+def test_full_size_launch_sampled_walkers_and_dets():
+    """56-orbital CAS(10e,10o) workload in the benchmark's launch configuration (4096 walkers, one
+    walker step per launch): sampled walkers' trajectories and local quantities against the oracle."""
+    P = _mrq()
+    s = S.workload("cas10_56o")
+    ctx = P.Context.from_system(s)
+    orc = O.Oracle.from_system(s)
+    nw, steps, seed = 4096, 2, 1000
+    p = ctx.params(nw, steps, burn_in=0, seed=seed, n_groups=16)
+    ctx.walkers_init(p)
+    for _ in range(steps):
+        ctx.walkers_advance(1)
+        ctx.finalize()
+    dets, _ = ctx.walkers(nw)
+    for w in (0, 4095):
+        traj = orc.walk_one(w, steps, seed)
+        assert np.array_equal(dets[w], traj[-1]), w
+    # local quantities at the start determinant and at one FOIS neighbour of it
+    r = orc.local(s.dets[orc.start], max_nb=1)
+    loc, _ = ctx.debug_local(s.dets[orc.start][None])
+    for key_g, key_o in (("S", "S"), ("e_local", "EL"), ("h_nn", "Hnn"), ("psi", "psi")):
+        assert close(loc[key_g][0], r[key_o]), key_g
+    assert loc["n_neighbours"][0] == r["nnb"] and loc["n_terms"][0] == r["terms"]
