@@ -214,6 +214,86 @@ int mrq_finalize(mrq_ctx* ctx, mrq_result* out);
 #define MRQ_NOALLOC_SCRATCH_DOUBLES (1 << 19)
 int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out);
 
+/*
+ * Batched walk: advance the walkers of n contexts (independent systems, each initialised with
+ * mrq_walkers_init) by n_steps in one walk launch per determinant width, so that many small
+ * systems fill the GPU together (the paper runs each system on its own; walkers are independent
+ * Markov chains, Sec. II B).  Walker ids, seeds and accumulators stay per context, so every
+ * trajectory is the same as when its context advances alone.  All contexts must be on one device;
+ * the launch uses ctxs[0]'s stream after waiting for every context's stream, and returns after it
+ * completes.  The walk time is reported by mrq_finalize on ctxs[0] only.
+ * Errors: MRQ_INVALID_ARG (null / duplicate contexts, different devices), MRQ_NOT_LOADED.
+ */
+int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps);
+
+/* mrq_walkers_init for each context (params[i]), mrq_batch_advance(params[0].n_steps), and
+ * mrq_finalize of each into out[i].  Every params[i].n_steps must be equal. */
+int mrq_sample_batch(mrq_ctx* const* ctxs, int n, const mrq_sample_params* params, mrq_result* out);
+
+/* ------------------------------------------------------------------------------------------
+ * Request server (serving form; the paper has no counterpart - it runs one system per job).
+ * Sampling requests for different systems wait in a FIFO queue; each scheduling round admits
+ * queued requests while the device-memory budget and the active-slot limit allow, advances all
+ * active requests together (mrq_batch_advance), finalizes them and retires those that reached
+ * their target sigma of E^(2) or their step limit.  A request's walkers take the same steps
+ * whatever else is active, so its trajectory is the same alone and in the mix.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct mrq_server mrq_server;
+
+enum mrq_request_state { MRQ_REQ_QUEUED = 0, MRQ_REQ_RUNNING = 1, MRQ_REQ_DONE = 2, MRQ_REQ_FAILED = 3,
+                         MRQ_REQ_CANCELLED = 4 };
+
+typedef struct {
+    int32_t device;
+    int32_t max_active;          /* requests resident at once */
+    int64_t hbm_budget_bytes;    /* device bytes the resident requests may use (estimated per request) */
+    int64_t steps_per_round;     /* walker steps per batched launch */
+} mrq_server_params;
+
+typedef struct {
+    int32_t n_core, n_act, n_virt, n_alpha, n_beta, reserved;
+    double e_core;
+    const double* h1;            /* as mrq_load_hamiltonian */
+    const double* eri;
+    int64_t n_det;               /* as mrq_load_reference */
+    const uint64_t* dets;
+    const double* coeffs;
+    int64_t n_labels;            /* 0: default coefficients; else as mrq_set_coeffs */
+    const double* c;
+    mrq_sample_params params;    /* n_walkers, burn_in, seed, n_groups, screen_tau (n_steps unused) */
+    double target_sigma;         /* stop when the jackknife sigma of E^(2) is at most this (0: never) */
+    int64_t max_steps;           /* stop after this many steps per walker */
+} mrq_request;
+
+typedef struct {
+    int32_t state;               /* mrq_request_state */
+    int32_t status;              /* mrq_status of a failed request */
+    int64_t steps_done;          /* steps per walker so far */
+    double queue_seconds;        /* submit -> admission */
+    double total_seconds;        /* submit -> done (or now) */
+    mrq_result result;           /* latest finalize (after every round while running) */
+} mrq_request_status;
+
+/* Create a server; nothing is loaded until requests are admitted. */
+int mrq_server_create(mrq_server** out, const mrq_server_params* p);
+/* Queue a request; the inputs are copied (the caller keeps ownership).  A request whose estimated
+ * footprint exceeds the whole budget is recorded as failed with MRQ_TOO_LARGE. */
+int mrq_server_submit(mrq_server* s, const mrq_request* req, int64_t* ticket);
+/* State, timings and latest result of a ticket. */
+int mrq_server_poll(mrq_server* s, int64_t ticket, mrq_request_status* out);
+/* Cancel a queued request at once, a running one at the end of the current round. */
+int mrq_server_cancel(mrq_server* s, int64_t ticket);
+/* Run one scheduling round on the calling thread (not while the background loop runs). */
+int mrq_server_step(mrq_server* s);
+/* Start / stop a background thread that runs rounds while there is work. */
+int mrq_server_start(mrq_server* s);
+int mrq_server_stop(mrq_server* s);
+/* out4 = queued, active, estimated resident bytes, walker steps advanced so far. */
+int mrq_server_info(mrq_server* s, int64_t* out4);
+const char* mrq_server_last_error(const mrq_server* s);
+/* Stop, free every resident request, destroy. */
+void mrq_server_destroy(mrq_server* s);
+
 /* mrq_walkers_init + mrq_walkers_advance(p->n_steps) + mrq_finalize. */
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out);
 

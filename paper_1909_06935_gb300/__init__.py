@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Context", "SampleParams", "Result", "Local", "Neighbour", "MRQError", "load_library", "NTYPES",
-           "TYPE_NAMES", "n_labels"]
+           "TYPE_NAMES", "n_labels", "batch_advance", "sample_batch"]
 
 NTYPES = 9
 TYPE_NAMES = ["CAS", "S_r", "S_rs", "S_i", "S_ir", "S_irs", "S_ij", "S_ijr", "S_ijrs"]   # index 3h + p
@@ -109,9 +109,11 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_sample.argtypes = [P, C.POINTER(SampleParams), C.POINTER(Result)]
     lib.mrq_read_accumulators.argtypes = [P, P, P, P, P, P]
     lib.mrq_read_walkers.argtypes = [P, P, P]
+    lib.mrq_batch_advance.argtypes = [P, C.c_int, I64]
+    lib.mrq_sample_batch.argtypes = [P, C.c_int, P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
-               "mrq_finalize_noalloc",
+               "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch",
                "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
@@ -256,3 +258,142 @@ class Context:
         psi = np.zeros(n_walkers)
         self._check(self._lib.mrq_read_walkers(self._h, _addr(d), _addr(psi)))
         return d, psi
+
+
+def _ctx_array(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c._h.value for c in ctxs])
+    return arr
+
+
+def batch_advance(ctxs, n_steps: int):
+    """Advance the walkers of several contexts together (one walk launch per determinant width)."""
+    lib = load_library()
+    rc = lib.mrq_batch_advance(C.cast(_ctx_array(ctxs), C.c_void_p), len(ctxs), n_steps)
+    if rc:
+        raise MRQError(rc, lib.mrq_last_error(ctxs[0]._h).decode())
+
+
+def sample_batch(ctxs, params):
+    """mrq_sample_batch: init, one batched advance, finalize each; returns the result dicts."""
+    lib = load_library()
+    n = len(ctxs)
+    parr = (SampleParams * n)(*params)
+    res = (Result * n)()
+    rc = lib.mrq_sample_batch(C.cast(_ctx_array(ctxs), C.c_void_p), n, C.cast(parr, C.c_void_p),
+                              C.cast(res, C.c_void_p))
+    if rc:
+        raise MRQError(rc, lib.mrq_last_error(ctxs[0]._h).decode())
+    return [r.as_dict() for r in res]
+
+
+# ------------------------------------------------------------------ request server
+
+class ServerParams(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_active", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("steps_per_round", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_core", C.c_int32), ("n_act", C.c_int32), ("n_virt", C.c_int32), ("n_alpha", C.c_int32),
+                ("n_beta", C.c_int32), ("reserved", C.c_int32), ("e_core", C.c_double), ("h1", C.c_void_p),
+                ("eri", C.c_void_p), ("n_det", C.c_int64), ("dets", C.c_void_p), ("coeffs", C.c_void_p),
+                ("n_labels", C.c_int64), ("c", C.c_void_p), ("params", SampleParams),
+                ("target_sigma", C.c_double), ("max_steps", C.c_int64)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("steps_done", C.c_int64),
+                ("queue_seconds", C.c_double), ("total_seconds", C.c_double), ("result", Result)]
+
+
+REQ_STATES = ["queued", "running", "done", "failed", "cancelled"]
+
+
+def _server_lib():
+    lib = load_library()
+    if not getattr(lib, "_server_typed", False):
+        P = C.c_void_p
+        lib.mrq_server_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(ServerParams)]
+        lib.mrq_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_int64)]
+        lib.mrq_server_poll.argtypes = [P, C.c_int64, C.POINTER(RequestStatus)]
+        lib.mrq_server_cancel.argtypes = [P, C.c_int64]
+        lib.mrq_server_step.argtypes = [P]
+        lib.mrq_server_start.argtypes = [P]
+        lib.mrq_server_stop.argtypes = [P]
+        lib.mrq_server_info.argtypes = [P, P]
+        lib.mrq_server_last_error.argtypes = [P]
+        lib.mrq_server_last_error.restype = C.c_char_p
+        lib.mrq_server_destroy.argtypes = [P]
+        lib.mrq_server_destroy.restype = None
+        for fn in ("mrq_server_create", "mrq_server_submit", "mrq_server_poll", "mrq_server_cancel",
+                   "mrq_server_step", "mrq_server_start", "mrq_server_stop", "mrq_server_info"):
+            getattr(lib, fn).restype = C.c_int
+        lib._server_typed = True
+    return lib
+
+
+class Server:
+    """Request server: continuous batching of sampling requests on one device."""
+
+    def __init__(self, device=0, max_active=16, hbm_budget_bytes=64 << 30, steps_per_round=1):
+        self._lib = _server_lib()
+        h = C.c_void_p()
+        rc = self._lib.mrq_server_create(C.byref(h), C.byref(ServerParams(device, max_active, hbm_budget_bytes,
+                                                                          steps_per_round)))
+        if rc:
+            raise MRQError(rc, "mrq_server_create failed")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mrq_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, s, n_walkers, max_steps, target_sigma=0.0, burn_in=0, seed=1, n_groups=16,
+               screen_tau=1e-10, c=None):
+        arrays = [np.ascontiguousarray(s.h1, np.float64), np.ascontiguousarray(s.eri, np.float64),
+                  np.ascontiguousarray(s.dets, np.uint64), np.ascontiguousarray(s.coeffs, np.float64),
+                  np.ascontiguousarray(s.c if c is None else c, np.float64)]
+        h1, eri, dets, co, cc = arrays
+        req = Request(s.n_core, s.n_act, s.n_virt, s.n_alpha, s.n_beta, 0, float(s.e_nuc), _addr(h1).value,
+                      _addr(eri).value, len(co), _addr(dets).value, _addr(co).value, len(cc), _addr(cc).value,
+                      SampleParams(n_walkers, 0, burn_in, seed, n_groups, 0, screen_tau, 0, 0),
+                      float(target_sigma), int(max_steps))
+        t = C.c_int64(0)
+        rc = self._lib.mrq_server_submit(self._h, C.byref(req), C.byref(t))
+        if rc:
+            raise MRQError(rc, "mrq_server_submit rejected the request")
+        return t.value
+
+    def poll(self, ticket):
+        st = RequestStatus()
+        rc = self._lib.mrq_server_poll(self._h, ticket, C.byref(st))
+        if rc:
+            raise MRQError(rc, "unknown ticket")
+        return dict(state=REQ_STATES[st.state], status=st.status, steps_done=st.steps_done,
+                    queue_seconds=st.queue_seconds, total_seconds=st.total_seconds, result=st.result.as_dict())
+
+    def cancel(self, ticket):
+        rc = self._lib.mrq_server_cancel(self._h, ticket)
+        if rc:
+            raise MRQError(rc, "unknown ticket")
+
+    def step(self):
+        rc = self._lib.mrq_server_step(self._h)
+        if rc:
+            raise MRQError(rc, self._lib.mrq_server_last_error(self._h).decode())
+
+    def start(self):
+        self._lib.mrq_server_start(self._h)
+
+    def stop(self):
+        self._lib.mrq_server_stop(self._h)
+
+    def info(self):
+        out = np.zeros(4, np.int64)
+        self._lib.mrq_server_info(self._h, out.ctypes.data_as(C.c_void_p))
+        return dict(queued=int(out[0]), active=int(out[1]), bytes=int(out[2]), walker_steps=int(out[3]))

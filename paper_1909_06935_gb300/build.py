@@ -6,8 +6,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(SRC_DIR, "mrq.cu")]
-DEPS = SOURCES + [os.path.join(SRC_DIR, "mrq_device.cuh"),
+SOURCES = [os.path.join(SRC_DIR, "mrq.cu"), os.path.join(SRC_DIR, "mrq_server.cpp")]
+DEPS = SOURCES + [os.path.join(SRC_DIR, "mrq_device.cuh"), os.path.join(SRC_DIR, "mrq_cas.cuh"),
                   os.path.join(os.path.dirname(HERE), "include", "mrq.h")]
 LIB = os.path.join(HERE, "_build", "libmrq.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -27,7 +27,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp] + SOURCES
+    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-Xcompiler", "-pthread", "-o", tmp] + SOURCES
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

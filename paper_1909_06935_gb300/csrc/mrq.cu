@@ -480,27 +480,50 @@ __device__ __forceinline__ void warp_smem(unsigned char* base, int cap, WarpSh*&
     ccode = reinterpret_cast<unsigned*>(cphi + cap);
 }
 
+// The walkers of one launch: one or several systems, each with its own walker array; slot numbers
+// run over all systems (system k owns slots [offsets[k], offsets[k+1])).
+struct WalkSet {
+    const SysDev* systems;
+    Walker* const* walkers;
+    const long long* offsets;
+    int nsys;
+    long long nslots;
+};
+
+__device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, int& sys, long long& local) {
+    int lo = 0, hi = ws.nsys - 1;
+    while (lo < hi) {                       // last system whose first slot is <= slot
+        const int mid = (lo + hi + 1) >> 1;
+        if (ws.offsets[mid] <= slot) lo = mid;
+        else hi = mid - 1;
+    }
+    sys = lo;
+    local = slot - ws.offsets[lo];
+}
+
 // One warp per walker slot.  Slot s advances walker order[s] (or s when order is null) by nsteps;
 // ordering the slots by determinant puts walkers that sit on the same determinant into
 // neighbouring warps, which then share cache lines (the results do not depend on the order).
 template <int W>
-__global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev* __restrict__ systems,
-                                                                   Walker* __restrict__ walkers, long long nslots,
-                                                                   int nsteps, int cap,
+__global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet ws, int nsteps, int cap,
                                                                    const unsigned* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long s0 = (long long)blockIdx.x * 4 + wi;
-    if (s0 >= nslots) return;
+    if (s0 >= ws.nslots) return;
     const long long slot = order ? (long long)order[s0] : s0;
+    int sys;
+    long long local;
+    slot_owner(ws, slot, sys, local);
+    Walker* const walkers = ws.walkers[sys];
     WarpSh* shp;
     double* cphi;
     unsigned* ccode;
     warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
     WarpSh& sh = *shp;
-    Walker wk = walkers[slot];
+    Walker wk = walkers[local];
     {
-        const int* src = reinterpret_cast<const int*>(systems + wk.sys);
+        const int* src = reinterpret_cast<const int*>(ws.systems + sys);
         int* dst = reinterpret_cast<int*>(&sh.sys);
         for (int k = lane; k < (int)(sizeof(SysDev) / sizeof(int)); k += 32) dst[k] = src[k];
         __syncwarp();
@@ -558,24 +581,26 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const SysDev*
 #pragma unroll
             for (int w = 0; w < W; w++) wk.d[sg][w] = n[sg][w];
         wk.psi = psin;
-        walkers[slot] = wk;
+        walkers[local] = wk;
     }
 }
 
 // sort key of a walker slot: system, label, then the active occupation (truncated), and the slot
 template <int W>
-__global__ void k_walker_keys(const SysDev* __restrict__ systems, const Walker* __restrict__ walkers,
-                              long long nslots, long long npad, unsigned long long* __restrict__ keys,
+__global__ void k_walker_keys(const WalkSet ws, long long npad, unsigned long long* __restrict__ keys,
                               unsigned* __restrict__ idx) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npad) return;
-    if (i >= nslots) {
+    if (i >= ws.nslots) {
         keys[i] = ~0ull;
         idx[i] = 0xFFFFFFFFu;
         return;
     }
-    const Walker wk = walkers[i];
-    const SysDev& S = systems[wk.sys];
+    int sys;
+    long long local;
+    slot_owner(ws, i, sys, local);
+    const Walker wk = ws.walkers[sys][local];
+    const SysDev& S = ws.systems[sys];
     unsigned long long d[2][W];
 #pragma unroll
     for (int sg = 0; sg < 2; sg++)
@@ -584,7 +609,7 @@ __global__ void k_walker_keys(const SysDev* __restrict__ systems, const Walker* 
     int h, p;
     const long long l = det_label<W>(S, d, h, p);
     const unsigned long long act = hash_key(S, active_bits<W>(S, d[0]), active_bits<W>(S, d[1]));
-    keys[i] = ((unsigned long long)(wk.sys & 0xFFFF) << 48) | ((unsigned long long)(l & 0xFFFFFF) << 24) |
+    keys[i] = ((unsigned long long)(sys & 0xFFFF) << 48) | ((unsigned long long)(l & 0xFFFFFF) << 24) |
               (act & 0xFFFFFFull);
     idx[i] = (unsigned)i;
 }
@@ -1261,6 +1286,15 @@ struct mrq_ctx {
     long long acc_lab = 0;
     int acc_G = 0;
     int* d_err = nullptr;
+    Walker** d_wptr = nullptr;                   // this context's walk set: one walker array
+    Walker* h_wset_ptr = nullptr;                // (host staging of the copies above)
+    long long h_wset_off[2] = {0, 0};
+    long long* d_woff = nullptr;
+    // batch tables (a batch launched through this context as the first of its list)
+    SysDev* d_bsys = nullptr;
+    Walker** d_bwptr = nullptr;
+    long long* d_boff = nullptr;
+    int bcap = 0;
     unsigned long long* d_sort_keys = nullptr;   // walker-slot ordering by determinant
     unsigned* d_sort_idx = nullptr;
     long long sort_cap = 0;
@@ -1359,12 +1393,12 @@ static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
     return 0;
 }
 
-// walk launch: order the slots by determinant (when the walker count allows a one-block sort),
-// then one warp per slot
-static int launch_walk(mrq_ctx* ctx, int W, const SysDev* d_systems, Walker* d_walkers, long long nslots, int nsteps,
-                       int cap) {
+// walk launch: order the slots by determinant (when the slot count allows a one-block sort),
+// then one warp per slot; `ctx` provides the stream and the sort scratch
+static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int cap) {
     const size_t smem = 4 * warp_smem_bytes(cap);
     const unsigned* order = nullptr;
+    const long long nslots = ws.nslots;
     if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
         long long npad = 1;
         while (npad < nslots) npad <<= 1;
@@ -1376,8 +1410,8 @@ static int launch_walk(mrq_ctx* ctx, int W, const SysDev* d_systems, Walker* d_w
             ctx->sort_cap = npad;
         }
         const unsigned nb = (unsigned)((npad + 255) / 256);
-        if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(d_systems, d_walkers, nslots, npad, ctx->d_sort_keys, ctx->d_sort_idx);
-        else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(d_systems, d_walkers, nslots, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+        if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+        else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
         const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
         CK(cudaFuncSetAttribute(k_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
         k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
@@ -1387,10 +1421,10 @@ static int launch_walk(mrq_ctx* ctx, int W, const SysDev* d_systems, Walker* d_w
     const unsigned blocks = (unsigned)((nslots + 3) / 4);
     if (W == 1) {
         CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(d_systems, d_walkers, nslots, nsteps, cap, order);
+        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(ws, nsteps, cap, order);
     } else {
         CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(d_systems, d_walkers, nslots, nsteps, cap, order);
+        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(ws, nsteps, cap, order);
     }
     CK(cudaGetLastError());
     return 0;
@@ -1440,6 +1474,11 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_res);
     dfree(ctx->d_sort_keys);
     dfree(ctx->d_sort_idx);
+    dfree(ctx->d_wptr);
+    dfree(ctx->d_woff);
+    dfree(ctx->d_bsys);
+    dfree(ctx->d_bwptr);
+    dfree(ctx->d_boff);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1776,6 +1815,17 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
     double c0 = 1.0;
     CK(cudaMemcpyAsync(&c0, ctx->d_c, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->d_wptr) {
+        CK(cudaMalloc(&ctx->d_wptr, sizeof(Walker*)));
+        CK(cudaMalloc(&ctx->d_woff, 2 * sizeof(long long)));
+    }
+    {
+        ctx->h_wset_ptr = ctx->d_walk;
+        ctx->h_wset_off[0] = 0;
+        ctx->h_wset_off[1] = ctx->nwalk;
+        CK(cudaMemcpyAsync(ctx->d_wptr, &ctx->h_wset_ptr, sizeof(Walker*), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_woff, ctx->h_wset_off, 2 * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    }
     k_walkers_init<<<(unsigned)((ctx->nwalk + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->d_walk, ctx->nwalk, ctx->start[0], ctx->start[1], ctx->start[2], ctx->start[3], c0 * ctx->start_c, 0, ctx->G);
     CK(cudaGetLastError());
@@ -1794,8 +1844,8 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
         ctx->evs.push_back(e);
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
-    if (int r = launch_walk(ctx, ctx->W, ctx->d_sys, ctx->d_walk, ctx->nwalk, (int)n_steps, ctx->hsys.cand_cap))
-        return r;
+    WalkSet ws{ctx->d_sys, ctx->d_wptr, ctx->d_woff, 1, ctx->nwalk};
+    if (int r = launch_walk(ctx, ctx->W, ws, (int)n_steps, ctx->hsys.cand_cap)) return r;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
     ctx->launches++;
@@ -1865,6 +1915,85 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
                     "%d (use mrq_finalize)", (long long)ctx->nlab, ctx->G, need, MRQ_NOALLOC_SCRATCH_DOUBLES);
     CK(cudaSetDevice(ctx->device));
     return finalize_with(ctx, out, g_noalloc_ptr[ctx->device], nchunk);
+}
+
+int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
+    if (!ctxs || n <= 0) return MRQ_INVALID_ARG;
+    mrq_ctx* lead = ctxs[0];
+    if (!lead) return MRQ_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i]) return fail(lead, MRQ_INVALID_ARG, "context %d is null", i);
+        if (ctxs[i]->device != lead->device)
+            return fail(lead, MRQ_INVALID_ARG, "contexts of one batch must share a device");
+        if (!ctxs[i]->ref || !ctxs[i]->d_walk || ctxs[i]->nwalk == 0)
+            return fail(lead, MRQ_NOT_LOADED, "context %d has no initialised walkers", i);
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return fail(lead, MRQ_INVALID_ARG, "context %d appears twice", i);
+    }
+    if (n_steps <= 0) return 0;
+    lead->err[0] = 0;
+    cudaError_t e0 = cudaSetDevice(lead->device);
+    if (e0 != cudaSuccess) return fail(lead, MRQ_CUDA_ERROR, "cudaSetDevice: %s", cudaGetErrorString(e0));
+    mrq_ctx* ctx = lead;   // for CK
+    for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
+    if (n > ctx->bcap) {
+        dfree(ctx->d_bsys);
+        dfree(ctx->d_bwptr);
+        dfree(ctx->d_boff);
+        CK(cudaMalloc(&ctx->d_bsys, sizeof(SysDev) * n));
+        CK(cudaMalloc(&ctx->d_bwptr, sizeof(Walker*) * n));
+        CK(cudaMalloc(&ctx->d_boff, sizeof(long long) * (n + 1)));
+        ctx->bcap = n;
+    }
+    // one launch per determinant width
+    for (int W = 1; W <= 2; W++) {
+        std::vector<SysDev> sys;
+        std::vector<Walker*> wp;
+        std::vector<long long> off(1, 0);
+        int cap = 1;
+        for (int i = 0; i < n; i++) {
+            if (ctxs[i]->W != W) continue;
+            sys.push_back(ctxs[i]->hsys);
+            wp.push_back(ctxs[i]->d_walk);
+            off.push_back(off.back() + ctxs[i]->nwalk);
+            cap = std::max(cap, ctxs[i]->hsys.cand_cap);
+        }
+        if (sys.empty()) continue;
+        const int k = (int)sys.size();
+        CK(cudaMemcpy(ctx->d_bsys, sys.data(), sizeof(SysDev) * k, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_bwptr, wp.data(), sizeof(Walker*) * k, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_boff, off.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice));
+        const size_t q = (size_t)ctx->launches * 2;
+        while (ctx->evs.size() < q + 2) {
+            cudaEvent_t ev;
+            CK(cudaEventCreate(&ev));
+            ctx->evs.push_back(ev);
+        }
+        CK(cudaEventRecord(ctx->evs[q], ctx->stream));
+        WalkSet ws{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, k, off.back()};
+        if (int r = launch_walk(ctx, W, ws, (int)n_steps, cap)) return r;
+        CK(cudaEventRecord(ctx->evs[q + 1], ctx->stream));
+        ctx->launches++;
+        CK(cudaStreamSynchronize(ctx->stream));   // the tables are reused by the next width
+    }
+    for (int i = 0; i < n; i++) ctxs[i]->total_steps += n_steps * ctxs[i]->nwalk;
+    return 0;
+}
+
+int mrq_sample_batch(mrq_ctx* const* ctxs, int n, const mrq_sample_params* params, mrq_result* out) {
+    if (!ctxs || n <= 0 || !params || !out) return MRQ_INVALID_ARG;
+    for (int i = 0; i < n; i++)
+        if (params[i].n_steps != params[0].n_steps)
+            return fail(ctxs[0], MRQ_INVALID_ARG, "all systems of a batch take the same number of steps");
+    for (int i = 0; i < n; i++)
+        if (int r = mrq_walkers_init(ctxs[i], &params[i])) return r;
+    if (int r = mrq_batch_advance(ctxs, n, params[0].n_steps)) return r;
+    int rc = 0;
+    for (int i = 0; i < n; i++) {
+        int r = mrq_finalize(ctxs[i], &out[i]);
+        if (r && !rc) rc = r;
+    }
+    return rc;
 }
 
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out) {
