@@ -47,6 +47,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
+    ap.add_argument("--n-systems", type=int, default=64)
+    ap.add_argument("--n-requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=20.0, help="request arrivals per second (served mode)")
+    ap.add_argument("--target-sigma", type=float, default=1e-3)
+    ap.add_argument("--req-walkers", type=int, default=512)
+    ap.add_argument("--req-max-steps", type=int, default=400)
+    ap.add_argument("--max-active", type=int, default=16)
+    ap.add_argument("--budget-gb", type=float, default=100.0)
     return ap.parse_args()
 
 
@@ -313,10 +322,102 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Plain (one system per launch) against batched (all systems in one launch) on the batched
+    workload: 64 seeded systems, 30-120 orbitals, CAS(6..10) references, walkers proportional to
+    reference size (32,768 in total)."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import synthetic as S
+    specs, walkers = S.batch_specs(args.n_systems)
+    t0 = time.perf_counter()
+    systems = S.make_systems(specs, processes=min(16, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t0
+    import torch
+    import paper_1909_06935_gb300 as P
+    dev = torch.device("cuda", 0)
+    ctxs = [P.Context.from_system(s) for s in systems]
+    params = [c.params(nw, 0, burn_in=0, seed=500 + k, n_groups=8) for k, (c, nw) in enumerate(zip(ctxs, walkers))]
+    total = sum(walkers)
+
+    def plain_step():
+        for c in ctxs:
+            c.walkers_advance(1)
+            c.finalize()
+
+    def batched_step():
+        P.batch_advance(ctxs, 1)
+        for c in ctxs:
+            c.finalize()
+
+    out = {}
+    for name, fn in (("plain", plain_step), ("batched", batched_step)):
+        for c, p in zip(ctxs, params):
+            c.walkers_init(p)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize(dev)
+        out[name] = total * args.steps / (time.perf_counter() - t0)
+    line = {"metric": METRIC, "mode": "batched", "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "plain": out["plain"], "batched": out["batched"],
+            "speedup": out["batched"] / out["plain"], "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batch{args.n_systems}", "systems": args.n_systems, "walkers": total,
+                       "orbitals": [s.n_orb for s in systems], "reference_dets": [len(s.coeffs) for s in systems],
+                       "generation_seconds": t_gen}}
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Poisson stream of sampling requests through the request server (continuous batching):
+    p50 / p99 time to the target error of E^(2), and throughput."""
+    import synthetic as S
+    import paper_1909_06935_gb300 as P
+    rng = np.random.Generator(np.random.PCG64(77))
+    base = dict(n_core=2, n_act=6, n_virt=16, n_alpha=5, n_beta=5, rank=72, seed=3301, chol_sigma=0.06)
+    pool = [S.workload("tiny_12o_cas4")]
+    pool += [S.make_system(2 + k % 3, 4 + 2 * (k % 2), 8 + 4 * k, 2 + k % 3 + (2 + k % 2), 2 + k % 3 + (2 + k % 2),
+                           rank=40 + 8 * k, seed=3400 + k, chol_sigma=0.06) for k in range(6)]
+    scan = S.scan_systems(base, n_points=10)
+    reqs = [pool[int(rng.integers(len(pool)))] for _ in range(args.n_requests - len(scan))] + scan
+    order = rng.permutation(len(reqs))
+    srv = P.Server(max_active=args.max_active, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), steps_per_round=2)
+    srv.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for k in order:
+        tickets.append(srv.submit(reqs[k], args.req_walkers, args.req_max_steps, target_sigma=args.target_sigma,
+                                  burn_in=10, seed=900 + int(k), n_groups=16))
+        time.sleep(rng.exponential(1.0 / args.rate))
+    while not all(srv.poll(t)["state"] in ("done", "failed", "cancelled") for t in tickets):
+        time.sleep(0.02)
+    wall = time.perf_counter() - t0
+    srv.stop()
+    st = [srv.poll(t) for t in tickets]
+    tt = np.array([x["total_seconds"] for x in st])
+    reached = np.array([x["result"]["e2_sigma"] <= args.target_sigma for x in st])
+    steps = sum(x["result"]["walker_steps"] for x in st)
+    line = {"metric": "time-to-target", "mode": "served", "unit": "s", "p50": float(np.percentile(tt, 50)),
+            "p99": float(np.percentile(tt, 99)), "requests": len(st), "reached_target": int(reached.sum()),
+            "throughput_req_per_s": len(st) / wall, "walker_steps_per_s": srv.info()["walker_steps"] / wall,
+            "accumulated_walker_steps": int(steps), "target_sigma": args.target_sigma, "arrival_rate": args.rate,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served", "request_walkers": args.req_walkers, "max_steps": args.req_max_steps,
+                       "max_active": args.max_active, "scan_points": len(scan)}}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_served(args)
     else:
         run_ours(args)
 

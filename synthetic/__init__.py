@@ -292,7 +292,7 @@ def _generalized_fock(h1, L, n_core, n_act, gamma):
     if n_act:
         gL = np.einsum("tu,ktu->k", gamma, L[:, a, a])
         F += np.einsum("k,kpq->pq", gL, L)
-        F -= 0.5 * np.einsum("kpt,tu,kuq->pq", L[:, :, a], gamma, L[:, a, :])
+        F -= 0.5 * np.einsum("kpt,tu,kuq->pq", L[:, :, a], gamma, L[:, a, :], optimize=True)
     return F
 
 
@@ -310,7 +310,7 @@ def semicanonicalize(h1, L, n_core, n_act, gamma):
     if n - n_core - n_act:
         _, U[v, v] = np.linalg.eigh(F[v, v])
     h1r = U.T @ h1 @ U
-    Lr = np.einsum("pi,kpq,qj->kij", U, L, U)
+    Lr = np.matmul(np.matmul(U.T, L), U)
     return 0.5 * (h1r + h1r.T), Lr
 
 
@@ -418,3 +418,59 @@ def workload(name: str) -> System:
     if name not in _CACHE:
         _CACHE[name] = make_system(**WORKLOADS[name])
     return _CACHE[name]
+
+
+# --------------------------------------------------------------------------- batched / served workloads
+
+def batch_specs(n_sys: int = 64, seed: int = 2409, total_walkers: int = 32768):
+    """Size distribution of the batched workload: 30-120 spatial orbitals, active spaces of 6, 8 or 10
+    orbitals at half filling (references of 400, 4,900 or 63,504 determinants), 2-10 core orbitals,
+    Cholesky rank 3n; walkers per system proportional to the reference size (at least 32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = []
+    for k in range(n_sys):
+        n = int(rng.integers(30, 121))
+        na = int(rng.choice([6, 8, 10], p=[0.5, 0.35, 0.15]))
+        nc = int(rng.integers(2, 11))
+        nv = n - nc - na
+        specs.append(dict(n_core=nc, n_act=na, n_virt=nv, n_alpha=nc + na // 2, n_beta=nc + na // 2,
+                          rank=3 * n, seed=seed + 100 * (k + 1), chol_sigma=0.05))
+    ndet = np.array([len(cas_strings(s["n_act"], s["n_act"] // 2)) ** 2 for s in specs], dtype=float)
+    walkers = np.maximum(32, np.round(total_walkers * ndet / ndet.sum())).astype(int)
+    return specs, walkers.tolist()
+
+
+def _make_from_spec(spec):
+    return make_system(**spec)
+
+
+def make_systems(specs, processes: int = 0):
+    """Generate several systems, in a spawn process pool when processes > 1."""
+    if processes and processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_make_from_spec, specs)
+    return [make_system(**s) for s in specs]
+
+
+def scan_systems(spec: dict, n_points: int = 10, lam_max: float = 0.1, seed: int = 7):
+    """A 'geometry scan': one orbital partition, Cholesky factors L(lambda) = L0 + lambda dL for
+    lambda in [0, lam_max], each with its own CAS-CI reference and semicanonical orbitals."""
+    sp = dict(spec)
+    nc, na, nv = sp["n_core"], sp["n_act"], sp["n_virt"]
+    h1, L0 = make_integrals(nc, na, nv, sp["rank"], sp["seed"], chol_sigma=sp.get("chol_sigma", 0.05))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dL = rng.normal(0.0, 1.0, L0.shape) * np.abs(L0).mean()
+    dL = 0.5 * (dL + np.transpose(dL, (0, 2, 1)))
+    out = []
+    nla, nlb = sp["n_alpha"] - nc, sp["n_beta"] - nc
+    for k in range(n_points):
+        lam = lam_max * k / max(n_points - 1, 1)
+        L = L0 + lam * dL
+        e, C, sa, sb, gamma = casci(h1, L, nc, na, nla, nlb)
+        h1r, Lr = semicanonicalize(h1, L, nc, na, gamma)
+        dets, coeffs = _to_dets(C, sa, sb, nc, nc + na + nv)
+        c = psi_s_coeffs(n_labels(nc, nv), seed + k)
+        out.append(System(nc, na, nv, sp["n_alpha"], sp["n_beta"], np.ascontiguousarray(h1r), pack_eri(Lr), 0.0,
+                          dets, coeffs, float(e), c, meta=dict(lam=lam, gamma=gamma, L=Lr)))
+    return out
