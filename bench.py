@@ -115,6 +115,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank walks its own independent walkers: a different Philox key per rank."""
+    return 1000 + rank
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's (all ranks run the same number of walker-steps)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job walker-steps/s: all ranks' units over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -194,7 +215,7 @@ def run_ours(args):
     ctx.load_reference(system.dets, system.coeffs)
     ctx.set_coeffs(system.c)
     nw, inner = args.walkers, args.inner
-    seed = 1000 + rank
+    seed = rank_seed(rank)
     p = ctx.params(nw, args.warmup * inner, burn_in=0, seed=seed, n_groups=16)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
@@ -225,18 +246,13 @@ def run_ours(args):
             flush.zero_()
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     # walk-kernel time of the timed launches (CUDA events recorded by the library on its stream)
     walk_s = res["seconds"] - (res_w["seconds"] if res_w else 0.0)
     walk_launches = res["walk_launches"] - (res_w["walk_launches"] if res_w else 0)
     snap1 = ctx.walkers(nw)[0]
     units = nw * inner * args.steps
-    value = world * units / (ms / 1e3)
+    value = job_rate(units, world, ms)
 
     # algorithmic work per walker-step, counted exactly by the debug kernel on walker snapshots taken
     # before and after the timed region: every reach-back term H_mk phi0(k) is one FP64 FMA (2 flops),

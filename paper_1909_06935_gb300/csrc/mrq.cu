@@ -465,7 +465,7 @@ __device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long 
 #include "mrq_cas.cuh"
 
 #ifndef MRQ_WALK_MIN_BLOCKS
-#define MRQ_WALK_MIN_BLOCKS 2
+#define MRQ_WALK_MIN_BLOCKS 3
 #endif
 
 // per-warp shared memory: WarpSh, then the CAS path's candidate list (phi0 values and codes)
@@ -814,15 +814,17 @@ __global__ void k_expand_eri(const double* __restrict__ eri, double* __restrict_
     }
 }
 
-// physicists' tables: T[p][q][r][s] = <pq|rs> = (pr|qs) and, after n^4 entries, <pq||rs>
+// physicists' tables on the (core+active) x (core+active) x (active+virtual) x (active+virtual)
+// block: T[p][q][r][s] = <pq|rs> = (pr|qs) and, after tab_half entries, <pq||rs>
 __global__ void k_build_tab(const SysDev* __restrict__ sys, double* __restrict__ tab) {
     const SysDev S = *sys;
-    const long long n = S.n, n4 = n * n * n * n;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(t % n), r = (int)((t / n) % n), q = (int)((t / (n * n)) % n), p = (int)(t / (n * n * n));
+    const long long a = S.nca, v = S.nav, half = a * a * v * v;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t % v) + S.nc, r = (int)((t / v) % v) + S.nc;
+        const int q = (int)((t / (v * v)) % a), p = (int)(t / (v * v * a));
         const double d = eri_g(S, p, r, q, s), x = eri_g(S, p, s, q, r);
         tab[t] = d;
-        tab[n4 + t] = d - x;
+        tab[half + t] = d - x;
     }
 }
 
@@ -1536,7 +1538,8 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     CK(cudaMalloc(&ctx->d_h1, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eri, sizeof(double) * ctx->neri));
     CK(cudaMalloc(&ctx->d_eri4, sizeof(double) * npair * n * n));
-    CK(cudaMalloc(&ctx->d_tab, sizeof(double) * 2 * (long long)n * n * n * n));
+    const long long nca = n_core + n_act, nav = n_act + n_virt;
+    CK(cudaMalloc(&ctx->d_tab, sizeof(double) * 2 * std::max(1LL, nca * nca * nav * nav)));
     CK(cudaMalloc(&ctx->d_hc, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eps, sizeof(double) * n));
     CK(cudaMalloc(&ctx->d_gamma, sizeof(double) * std::max(1, n_act * n_act)));
@@ -1565,6 +1568,9 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     s.eri = ctx->d_eri;
     s.eri4 = ctx->d_eri4;
     s.tab = ctx->d_tab;
+    s.nca = (int)nca;
+    s.nav = (int)nav;
+    s.tab_half = (unsigned)(nca * nca * nav * nav);
     s.h1 = ctx->d_h1;
     s.hc = ctx->d_hc;
     s.eps = ctx->d_eps;

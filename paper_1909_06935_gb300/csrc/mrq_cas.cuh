@@ -206,17 +206,18 @@ __device__ __forceinline__ void dbl_entry(const SysDev& S, const unsigned long l
     const int sA0 = A0 >= n, sA1 = A1 >= n, sR0 = R0 >= n, sR1 = R1 >= n;
     const bool same = sA0 == sA1 && sR0 == sR1 && sA0 == sR0;
     const bool xpat = !same && sA0 != sR0;              // the allowed pairing is (A0,R1)(A1,R0)
-    const unsigned nn = (unsigned)n, n2 = nn * nn, n3 = n2 * nn;
+    // strides of T[p][q][r][s] on the (core+active)^2 x (active+virtual)^2 block
+    const unsigned sv = (unsigned)S.nav, sq = sv * sv, sp = sq * (unsigned)S.nca;
     const unsigned pA0 = (unsigned)(A0 - sA0 * n), pA1 = (unsigned)(A1 - sA1 * n);
-    const unsigned pR0 = (unsigned)(R0 - sR0 * n), pR1 = (unsigned)(R1 - sR1 * n);
-    unsigned base = same ? n3 * nn : 0u;
-    if (nf >= 1) base += pA0 * n3;
-    if (nf == 2) base += pA1 * n2;
+    const unsigned pR0 = (unsigned)(R0 - sR0 * n - S.nc), pR1 = (unsigned)(R1 - sR1 * n - S.nc);
+    unsigned base = same ? S.tab_half : 0u;
+    if (nf >= 1) base += pA0 * sp;
+    if (nf == 2) base += pA1 * sq;
     if (!xpat) {
-        if (ne >= 1) base += pR0 * nn;
+        if (ne >= 1) base += pR0 * sv;
         if (ne == 2) base += pR1;
     } else {
-        if (ne == 2) base += pR1 * nn;
+        if (ne == 2) base += pR1 * sv;
         if (ne >= 1) base += pR0;
     }
     const int odd = c1 + c2 + piA + piR + (xpat ? 1 : 0) + par_ref;
@@ -227,12 +228,12 @@ __device__ __forceinline__ void dbl_entry(const SysDev& S, const unsigned long l
 // a lane's table offsets for the direct and the swapped removed-pair layouts, and its core parity
 __device__ __forceinline__ void lane_offsets(const SysDev& S, int c, int v, int xc0, int xc1, int yv0, int yv1,
                                              unsigned& off_d, unsigned& off_x, int& par) {
-    const unsigned nn = (unsigned)S.n, n2 = nn * nn, n3 = n2 * nn;
+    const unsigned sv = (unsigned)S.nav, sq = sv * sv, sp = sq * (unsigned)S.nca;
     const unsigned p0 = (unsigned)(xc0 % S.n), p1 = (unsigned)(xc1 % S.n);
-    const unsigned v0 = (unsigned)(yv0 % S.n), v1 = (unsigned)(yv1 % S.n);
-    const unsigned core = c == 2 ? p0 * n3 + p1 * n2 : (c == 1 ? p0 * n2 : 0u);
-    off_d = core + (v == 2 ? v0 * nn + v1 : (v == 1 ? v0 : 0u));
-    off_x = core + (v == 2 ? v1 * nn + v0 : (v == 1 ? v0 * nn : 0u));
+    const unsigned v0 = (unsigned)(yv0 % S.n - S.nc), v1 = (unsigned)(yv1 % S.n - S.nc);
+    const unsigned core = c == 2 ? p0 * sp + p1 * sq : (c == 1 ? p0 * sq : 0u);
+    off_d = core + (v == 2 ? v0 * sv + v1 : (v == 1 ? v0 : 0u));
+    off_x = core + (v == 2 ? v1 * sv + v0 : (v == 1 ? v0 * sv : 0u));
     par = (c >= 1 ? (int)p0 : 0) + (c == 2 ? (int)p1 : 0);
 }
 

@@ -35,7 +35,12 @@ struct SysDev {
     unsigned long long mcore[2], mact[2], mvirt[2];   // orbital masks per word (same for both spins)
     const double* eri;      // packed (input layout)
     const double* eri4;     // half-unpacked: E[P(p,q)][r][s] = (pq|rs), n(n+1)/2 x n x n
-    const double* tab;      // 2 n^4: T[p][q][r][s] = <pq|rs> = (pr|qs), then <pq||rs> = (pr|qs) - (ps|qr)
+    // physicists' tables over the blocks the CAS path reads: p, q in core+active (nca), r, s in
+    // active+virtual (nav, index minus n_core): T[p][q][r][s] = <pq|rs> = (pr|qs), then, after
+    // tab_half entries, <pq||rs> = (pr|qs) - (ps|qr)
+    const double* tab;
+    int nca, nav;
+    unsigned tab_half;
     const double* hc;       // n*n: h_pq + sum_i [2(pq|ii) - (pi|iq)] (full core)
     const double* h1;       // n*n
     const double* eps;      // n: generalised-Fock diagonal

@@ -63,7 +63,8 @@ int64_t footprint_of(const Request& r) {
     while (cap < 2 * (int64_t)r.coeffs.size()) cap <<= 1;
     const int64_t G = std::max<int32_t>(r.params.n_groups, 1);
     int64_t b = 0;
-    b += 8 * (2 * n * n + neri + npair * n * n + 2 * n * n * n * n + n + r.n_act * r.n_act);
+    const int64_t nca = r.n_core + r.n_act, nav = r.n_act + r.n_virt;
+    b += 8 * (2 * n * n + neri + npair * n * n + 2 * nca * nca * nav * nav + n + r.n_act * r.n_act);
     b += 16 * cap + 8 * nlab;
     b += 16 * G * nlab + 16 * G;
     b += 64 * r.params.n_walkers + 16 * 8192;
