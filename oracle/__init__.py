@@ -9,8 +9,10 @@ Layers:
     perturber labels, reference lookup, reach-back overlaps <m|H|phi0> (Eq. 6-7), the local
     quantities of one walker step (Eq. 5, Eq. 16), the continuous-time walk, and brute-force
     deterministic strongly contracted quantities over the whole FOIS (Eq. 2, 14).
-  * this module: ctypes marshalling, and the finalize step (Eq. 14-15 with screening,
-    jackknife error bars) written with numpy directly from the equations.
+  * this module: ctypes marshalling, the finalize step (Eq. 14-15 with screening, jackknife
+    error bars), the SC-MRCI(s) energy gradient (Eq. 8-9), its exact counterpart and the
+    SC-MRCI eigenproblem in the basis of strongly contracted states, and the AMSGrad update
+    (Reddi, Kale, Kumar 2018), written with numpy directly from the equations.
 """
 from __future__ import annotations
 
@@ -65,9 +67,9 @@ def _load():
             lib.oracle_move.argtypes = [P, P, C.c_uint64, C.c_uint32, C.c_uint32, P, P]
             lib.oracle_sample.restype = C.c_int
             lib.oracle_sample.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int, C.c_int,
-                                          P, P, P, P, P, P]
+                                          P, P, P, P, P, P, P, P]
             lib.oracle_brute.restype = C.c_int
-            lib.oracle_brute.argtypes = [P, P, P, P]
+            lib.oracle_brute.argtypes = [P, P, P, P, P]
             lib.oracle_philox.argtypes = [P, P, P]
             lib.oracle_walk_one.restype = C.c_int
             lib.oracle_walk_one.argtypes = [P, C.c_uint32, C.c_int64, C.c_uint64, P]
@@ -195,13 +197,15 @@ class Oracle:
         accW = np.zeros(G)
         accE = np.zeros(G)
         ts = np.zeros(N_TYPES, np.int64)
+        accA = np.zeros((G, L))
+        accB = np.zeros((G, L))
         traj = np.zeros((n_walkers, n_steps, 2 * self.W), np.uint64) if trajectory else None
         rc = self._lib.oracle_sample(self._h, n_walkers, n_steps, burn_in, seed, G, threads, _ptr(accN),
-                                     _ptr(accU), _ptr(accW), _ptr(accE), _ptr(ts),
+                                     _ptr(accU), _ptr(accW), _ptr(accE), _ptr(ts), _ptr(accA), _ptr(accB),
                                      _ptr(traj) if trajectory else None)
         if rc:
             raise RuntimeError(f"oracle_sample failed with status {rc}")
-        acc = dict(N=accN, U=accU, W=accW, E=accE, type_steps=ts,
+        acc = dict(N=accN, U=accU, W=accW, E=accE, A=accA, B=accB, type_steps=ts,
                    walker_steps=n_walkers * max(n_steps - burn_in, 0))
         if trajectory:
             acc["trajectory"] = traj
@@ -211,13 +215,18 @@ class Oracle:
         return finalize(acc, self.e0, self.c, self.n_core, self.n_virt, tau)
 
     # ---- deterministic brute force
-    def brute(self):
-        """Deterministic SC quantities: N_l, D_l = <v_l|H_D|v_l>, <psi_s|psi_s>, <psi_s|H|psi_s>."""
+    def brute(self, label_matrix: bool = False):
+        """Deterministic SC quantities: N_l, D_l = <v_l|H_D|v_l>, <psi_s|psi_s>, <psi_s|H|psi_s>;
+        with label_matrix, also H_ll' = <v_l|H|v_l'> (dense; tiny systems only)."""
         Nl = np.zeros(self.n_labels)
         Dl = np.zeros(self.n_labels)
         out = np.zeros(3)
-        self._lib.oracle_brute(self._h, _ptr(Nl), _ptr(Dl), _ptr(out))
-        return dict(N=Nl, D=Dl, psi_norm=out[0], psi_H_psi=out[1], fois_size=int(out[2]))
+        Hll = np.zeros((self.n_labels, self.n_labels)) if label_matrix else None
+        self._lib.oracle_brute(self._h, _ptr(Nl), _ptr(Dl), _ptr(out), _ptr(Hll) if label_matrix else None)
+        r = dict(N=Nl, D=Dl, psi_norm=out[0], psi_H_psi=out[1], fois_size=int(out[2]))
+        if label_matrix:
+            r["H"] = Hll
+        return r
 
 
 # ------------------------------------------------------------------ finalize (Eq. 14-15)
@@ -303,3 +312,71 @@ def exact_from_brute(br, e0, c, n_core, n_virt, tau=1e-10):
         a0sq=c[0] ** 2 * N[0] / br["psi_norm"],
         rho_label=(c ** 2) * N / br["psi_norm"],
     )
+
+
+# ------------------------------------------------------------------ SC-MRCI(s) optimisation (Sec. II B)
+
+def mrci_gradient(acc):
+    """Sampled energy gradient of Eq. 8 with the derivative overlaps of Eq. 9,
+    g_l = < delta_{l,l_n} / c_l (E_L(n) - E) >, E = <E_L>, from the walk's residence-weighted
+    sums A_l = sum w E_L / c_l and B_l = sum w / c_l (all groups).  Like Eq. 8 it leaves out the
+    factor 2 of d(<psi|H|psi>/<psi|psi>)/dc_l for a real psi.  Returns (g, E)."""
+    Wt, Et = acc["W"].sum(), acc["E"].sum()
+    E = Et / Wt
+    return (acc["A"].sum(0) - E * acc["B"].sum(0)) / Wt, E
+
+
+def mrci_gradient_groups(acc):
+    """The sampled gradient and its jackknife error over the walker groups."""
+    A, B, W, E = acc["A"], acc["B"], acc["W"], acc["E"]
+    G = A.shape[0]
+    g, _ = mrci_gradient(acc)
+    if G < 2:
+        return g, np.full_like(g, np.nan)
+    At, Bt, Wt, Et = A.sum(0), B.sum(0), W.sum(), E.sum()
+    jk = []
+    for k in range(G):
+        e = (Et - E[k]) / (Wt - W[k])
+        jk.append((At - A[k] - e * (Bt - B[k])) / (Wt - W[k]))
+    jk = np.array(jk)
+    return g, np.sqrt((G - 1) / G * ((jk - jk.mean(0)) ** 2).sum(0))
+
+
+def exact_gradient(br, c):
+    """Exact value of the same gradient for psi = sum_l c_l v_l from the label Hamiltonian
+    H_ll' = <v_l|H|v_l'> and the diagonal overlap N_l = <v_l|v_l>:
+    g = (H c - E N c) / (c^T N c), E = c^T H c / c^T N c.  Returns (g, E)."""
+    H, N = br["H"], br["N"]
+    nrm = c @ (N * c)
+    E = c @ (H @ c) / nrm
+    return (H @ c - E * N * c) / nrm, E
+
+
+def sc_mrci(br):
+    """SC-MRCI eigenproblem in the basis of strongly contracted states (Sec. II B): the lowest
+    root of H c = E N c over the labels with N_l > 0.  Returns (E, c) with c_0 = 1."""
+    H, N = br["H"], br["N"]
+    keep = np.nonzero(N > 0)[0]
+    s = 1.0 / np.sqrt(N[keep])
+    Ht = s[:, None] * H[np.ix_(keep, keep)] * s[None, :]
+    w, V = np.linalg.eigh(0.5 * (Ht + Ht.T))
+    c = np.zeros(len(N))
+    c[keep] = s * V[:, 0]
+    return w[0], c / c[0]
+
+
+def amsgrad(c, g, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AMSGrad step (Reddi, Kale, Kumar, ICLR 2018, their Algorithm 2, no bias correction)
+    on c_l for l >= 1, with eps in the denominator; c_0 stays fixed.  `state` holds m, v, vhat
+    (zero at the start) and is updated in place.  Returns the new c."""
+    m, v, vh = state["m"], state["v"], state["vhat"]
+    m[1:] = beta1 * m[1:] + (1 - beta1) * g[1:]
+    v[1:] = beta2 * v[1:] + (1 - beta2) * g[1:] ** 2
+    vh[1:] = np.maximum(vh[1:], v[1:])
+    c = c.copy()
+    c[1:] -= lr * m[1:] / (np.sqrt(vh[1:]) + eps)
+    return c
+
+
+def amsgrad_state(n):
+    return dict(m=np.zeros(n), v=np.zeros(n), vhat=np.zeros(n))

@@ -627,11 +627,13 @@ uint32_t oracle_move(void *h, const uint64_t *x, uint64_t seed, uint32_t step, u
  *   accU[g*nlab + l] += w num / c_l^2     (H_D numerator, Eq. 16; l > 0)
  *   accW[g] += w, accE[g] += w E_L        (Eq. 4)
  *   type_steps[t] += 1 for the walker's type t = 3h + p
+ *   accA[g*nlab + l] += w E_L / c_l, accB[g*nlab + l] += w / c_l   (optional; the SC-MRCI(s)
+ *       energy gradient, Eq. 8-9: <n|psi_l>/<n|psi> = delta_{l,l_n} / c_l)
  * traj (optional) receives the determinant after every step (nwalk x nsteps x 2W words).
  * Returns 0, or -4 when a walker has no move (S = 0). */
 int oracle_sample(void *h, int64_t nwalk, int64_t nsteps, int64_t burn, uint64_t seed, int G,
                   int nthreads, double *accN, double *accU, double *accW, double *accE,
-                  int64_t *type_steps, uint64_t *traj) {
+                  int64_t *type_steps, double *accA, double *accB, uint64_t *traj) {
     osys *S = (osys *)h;
     int64_t nrec = nsteps > burn ? nsteps - burn : 0;
     int64_t tot = nwalk * nrec;
@@ -669,6 +671,8 @@ int oracle_sample(void *h, int64_t nwalk, int64_t nsteps, int64_t burn, uint64_t
                 if (l > 0) accU[g * S->nlab + l] += rw[r] * rn[r] / c2;
                 accW[g] += rw[r];
                 accE[g] += rw[r] * re[r];
+                if (accA) accA[g * S->nlab + l] += rw[r] * re[r] / S->c[l];
+                if (accB) accB[g * S->nlab + l] += rw[r] / S->c[l];
                 type_steps[rt[r]] += 1;
             }
         }
@@ -696,7 +700,10 @@ int oracle_walk_one(void *h, uint32_t walker, int64_t nsteps, uint64_t seed, uin
  *   v_l = P_l H phi0 (Eq. 2): apply H to every reference determinant, bucket by label;
  *   N_l = <v_l|v_l>, D_l = <v_l|H_D|v_l> (Eq. 14 numerator), and for the sampling function
  *   psi_s = c_0 phi0 + sum_l c_l v_l: <psi_s|psi_s> and <psi_s|H|psi_s>.
- * Sizes: Nl[nlab], Dl[nlab], out[0] = <psi_s|psi_s>, out[1] = <psi_s|H|psi_s>, out[2] = FOIS size. */
+ * Sizes: Nl[nlab], Dl[nlab], out[0] = <psi_s|psi_s>, out[1] = <psi_s|H|psi_s>, out[2] = FOIS size.
+ * Hll (optional, nlab x nlab row-major) receives the SC-MRCI(s) Hamiltonian in the basis of the
+ * strongly contracted states, Hll[l][l'] = <v_l|H|v_l'> with v_0 = phi0 (Sec. II B); their
+ * overlap matrix is diagonal, diag(Nl), because different labels never share a determinant. */
 
 typedef struct { det_t d; double v; } dv_t;
 
@@ -711,7 +718,7 @@ static int64_t find_dv(const dv_t *a, int64_t n, const det_t *d) {
     return -1;
 }
 
-int oracle_brute(void *h, double *Nl, double *Dl, double *out) {
+int oracle_brute(void *h, double *Nl, double *Dl, double *out, double *Hll) {
     osys *S = (osys *)h;
     int n = S->n;
     /* 1. collect every determinant H-connected to a reference determinant, outside the CAS */
@@ -746,6 +753,7 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out) {
     }
     memset(Nl, 0, sizeof(double) * S->nlab);
     memset(Dl, 0, sizeof(double) * S->nlab);
+    if (Hll) memset(Hll, 0, sizeof(double) * S->nlab * S->nlab);
     Nl[0] = S->norm0;
     Dl[0] = S->e0 * S->norm0;
     double pp = S->c[0] * S->c[0] * S->norm0, php = 0.0;
@@ -769,6 +777,12 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out) {
         double dl = 0.0, ph = 0.0;
         if (li > 0) dl += hd_diag(S, &d) * vi * vi;
         ph += ci * vi * h_diag(S, &d) * ci * vi;
+        if (Hll) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            Hll[li * S->nlab + li] += vi * h_diag(S, &d) * vi;
+        }
         int occl[2 * MAXN], empl[2 * MAXN], no = 0, ne = 0;
         for (int so = 0; so < 2 * n; so++) { if (occ(&d, so, n)) occl[no++] = so; else empl[ne++] = so; }
         for (int kind = 1; kind <= 2; kind++)
@@ -786,6 +800,12 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out) {
                             else { int64_t j = find_dv(buf, u, &m); vm = j >= 0 ? buf[j].v : 0.0; }
                             if (vm == 0.0) continue;
                             ph += ci * vi * h_elem(S, &d, &m) * S->c[lm] * vm;
+                            if (Hll) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                                Hll[li * S->nlab + lm] += vi * h_elem(S, &d, &m) * vm;
+                            }
                             if (li > 0 && lm == li) dl += vi * hd_elem(S, &d, &m) * vm;
                         }
         dla[i + S->nref] = dl;
