@@ -304,6 +304,34 @@ int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out);
 int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW, double* accE,
                           int64_t* type_steps);
 
+/*
+ * SC-MRCI(s) energy gradient of the last walk (Eq. 8-9, Sec. II B): for the sampled function
+ * psi = sum_l c_l psi_l, <n|d psi/d c_l> / <n|psi> = delta_{l,l_n} / c_l, so
+ *   grad[l] = < delta_{l,l_n} / c_l (E_L(n) - E) >,  E = <E_L>,
+ * averaged with the walk's residence weights over all groups.  Like Eq. 8 it leaves out the
+ * factor 2 of the derivative of <psi|H|psi>/<psi|psi> for a real psi.  grad receives n_labels
+ * doubles (host or device memory, or NULL), energy the estimate E (or NULL).
+ * Errors: MRQ_NOT_LOADED (no walk since the reference was loaded).
+ */
+int mrq_mrci_gradient(mrq_ctx* ctx, double* grad, double* energy);
+
+/*
+ * One AMSGrad step (Reddi, Kale, Kumar, ICLR 2018, without bias correction; the optimiser of
+ * Sec. II B) on the context's coefficients c_l, l >= 1, with the gradient of the last
+ * mrq_mrci_gradient call:  m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,  vhat = max(vhat, v),
+ * c -= lr m / (sqrt(vhat) + eps).  c_0 stays fixed: the energy does not depend on the scale of c.
+ * m, v, vhat live on the device, start at zero and are reset by mrq_set_coeffs.
+ * Errors: MRQ_NOT_LOADED (no gradient yet), MRQ_INVALID_ARG (lr <= 0, beta outside [0,1), eps <= 0).
+ */
+int mrq_amsgrad_step(mrq_ctx* ctx, double lr, double beta1, double beta2, double eps);
+
+/* Current coefficients c_l (n_labels doubles, host or device memory). */
+int mrq_read_coeffs(mrq_ctx* ctx, double* c);
+
+/* Raw gradient sums of the last walk per walker group, n_groups x n_labels doubles each (host
+ * memory; either may be NULL): accA[g][l] = sum w E_L / c_l, accB[g][l] = sum w / c_l. */
+int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB);
+
 /* Walker determinants (n_walkers x 2W words) and psi_s values; either may be NULL. */
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi);
 

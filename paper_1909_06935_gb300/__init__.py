@@ -110,11 +110,15 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_read_accumulators.argtypes = [P, P, P, P, P, P]
     lib.mrq_read_walkers.argtypes = [P, P, P]
     lib.mrq_batch_advance.argtypes = [P, C.c_int, I64]
+    lib.mrq_mrci_gradient.argtypes = [P, P, P]
+    lib.mrq_amsgrad_step.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double]
+    lib.mrq_read_coeffs.argtypes = [P, P]
+    lib.mrq_read_gradient_sums.argtypes = [P, P, P]
     lib.mrq_sample_batch.argtypes = [P, C.c_int, P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
-               "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch",
-               "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
+               "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch", "mrq_mrci_gradient",
+               "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -252,6 +256,42 @@ class Context:
         ts = np.zeros(NTYPES, np.int64)
         self._check(self._lib.mrq_read_accumulators(self._h, _addr(N), _addr(U), _addr(Wg), _addr(E), _addr(ts)))
         return dict(N=N, U=U, W=Wg, E=E, type_steps=ts)
+
+    def mrci_gradient(self):
+        """SC-MRCI(s) gradient (Eq. 8-9) of the last walk and the energy estimate."""
+        g = np.zeros(self.n_labels)
+        e = C.c_double(0.0)
+        self._check(self._lib.mrq_mrci_gradient(self._h, _addr(g), C.byref(e)))
+        return g, e.value
+
+    def amsgrad_step(self, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8):
+        """One AMSGrad update of the device coefficients from the last gradient."""
+        self._check(self._lib.mrq_amsgrad_step(self._h, lr, beta1, beta2, eps))
+
+    def coeffs(self):
+        c = np.zeros(self.n_labels)
+        self._check(self._lib.mrq_read_coeffs(self._h, _addr(c)))
+        return c
+
+    def gradient_sums(self, n_groups: int):
+        """Per-group sums A[g, l] = sum w E_L / c_l and B[g, l] = sum w / c_l of the last walk."""
+        a = np.zeros((n_groups, self.n_labels))
+        b = np.zeros((n_groups, self.n_labels))
+        self._check(self._lib.mrq_read_gradient_sums(self._h, _addr(a), _addr(b)))
+        return a, b
+
+    def optimize_mrci(self, n_iter, n_walkers, n_steps, burn_in=20, lr=0.01, seed=1, n_groups=8,
+                      beta1=0.9, beta2=0.999, eps=1e-8):
+        """SC-MRCI(s) by AMSGrad (Sec. II B): each iteration walks psi = sum_l c_l psi_l with the
+        current coefficients, takes the sampled gradient and updates c on the device.  Returns the
+        result of every iteration's walk (its e_var is the energy of the c it walked with)."""
+        hist = []
+        for it in range(n_iter):
+            res = self.sample(self.params(n_walkers, n_steps, burn_in=burn_in, seed=seed + it, n_groups=n_groups))
+            self.mrci_gradient()
+            self.amsgrad_step(lr, beta1, beta2, eps)
+            hist.append(res)
+        return hist
 
     def walkers(self, n_walkers: int):
         d = np.zeros((n_walkers, 2 * self.W), np.uint64)

@@ -565,6 +565,8 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet
             if (ln > 0) atomicAdd(S.accU + base + ln, (w * lo.num) / c2);
             atomicAdd(S.accW + wk.group, w);
             atomicAdd(S.accE + wk.group, w * lo.EL);
+            atomicAdd(S.accA + base + ln, (w * lo.EL) / cl);
+            atomicAdd(S.accB + base + ln, w / cl);
             atomicAdd(S.type_steps + 3 * h + p, 1ull);
         }
 #pragma unroll
@@ -1238,6 +1240,45 @@ __global__ void k_fin_reduce(const SysDev* __restrict__ sys, const double* parti
     res->walker_steps = wsteps;
 }
 
+// ============================================================================ SC-MRCI(s) optimisation (Eq. 8-9)
+
+// grad[l] = (A_l - E B_l) / W over all groups, E = sum E / sum W: <delta_{l,l_n}/c_l (E_L - E)>
+__global__ void k_mrci_grad(const SysDev* __restrict__ sys, double* __restrict__ grad, double* __restrict__ energy) {
+    const SysDev S = *sys;
+    double Wt = 0.0, Et = 0.0;
+    for (int g = 0; g < S.G; g++) {
+        Wt += S.accW[g];
+        Et += S.accE[g];
+    }
+    const double E = Et / Wt;
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < S.nlab; l += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int g = 0; g < S.G; g++) {
+            a += S.accA[(long long)g * S.nlab + l];
+            b += S.accB[(long long)g * S.nlab + l];
+        }
+        grad[l] = (a - E * b) / Wt;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *energy = E;
+}
+
+// AMSGrad (Reddi, Kale, Kumar, ICLR 2018) on c_l, l >= 1; c_0 stays fixed (the energy does not
+// depend on the overall scale of c)
+__global__ void k_amsgrad(double* __restrict__ c, const double* __restrict__ g, double* __restrict__ m,
+                          double* __restrict__ v, double* __restrict__ vh, long long nlab, double lr, double b1,
+                          double b2, double eps) {
+    for (long long l = 1 + (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nlab; l += (long long)gridDim.x * blockDim.x) {
+        const double gl = g[l];
+        const double ml = b1 * m[l] + (1.0 - b1) * gl;
+        const double vl = b2 * v[l] + (1.0 - b2) * gl * gl;
+        const double vhl = fmax(vh[l], vl);
+        m[l] = ml;
+        v[l] = vl;
+        vh[l] = vhl;
+        c[l] -= lr * ml / (sqrt(vhl) + eps);
+    }
+}
+
 // ============================================================================ fixed scratch for mrq_finalize_noalloc
 //
 // Partial sums of the finalize kernels for callers that cannot allocate device memory.  Every
@@ -1284,6 +1325,8 @@ struct mrq_ctx {
     unsigned long long seed = 0;
     double tau = 1e-10;
     double *d_accN = nullptr, *d_accU = nullptr, *d_accW = nullptr, *d_accE = nullptr;
+    double *d_accA = nullptr, *d_accB = nullptr;        // SC-MRCI gradient sums [G][nlab]
+    double *d_grad = nullptr, *d_am_m = nullptr, *d_am_v = nullptr, *d_am_vh = nullptr;   // AMSGrad state
     unsigned long long* d_types = nullptr;
     long long acc_lab = 0;
     int acc_G = 0;
@@ -1346,6 +1389,12 @@ static void free_walkers(mrq_ctx* c) {
     dfree(c->d_walk);
     dfree(c->d_accN);
     dfree(c->d_accU);
+    dfree(c->d_accA);
+    dfree(c->d_accB);
+    dfree(c->d_grad);
+    dfree(c->d_am_m);
+    dfree(c->d_am_v);
+    dfree(c->d_am_vh);
     dfree(c->d_accW);
     dfree(c->d_accE);
     dfree(c->d_types);
@@ -1370,6 +1419,8 @@ static int push_sys(mrq_ctx* ctx) {
     SysDev& s = ctx->hsys;
     s.accN = ctx->d_accN;
     s.accU = ctx->d_accU;
+    s.accA = ctx->d_accA;
+    s.accB = ctx->d_accB;
     s.accW = ctx->d_accW;
     s.accE = ctx->d_accE;
     s.type_steps = ctx->d_types;
@@ -1718,6 +1769,9 @@ int mrq_set_coeffs(mrq_ctx* ctx, int64_t n_labels, const double* c) {
     if (n_labels != ctx->nlab || !c)
         return fail(ctx, MRQ_INVALID_ARG, "expected %lld coefficients", (long long)ctx->nlab);
     CK(cudaSetDevice(ctx->device));
+    dfree(ctx->d_am_m);     // a new coefficient vector starts a new optimisation
+    dfree(ctx->d_am_v);
+    dfree(ctx->d_am_vh);
     CK(cudaMemcpyAsync(ctx->d_c, c, sizeof(double) * n_labels, cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return 0;
@@ -1796,6 +1850,10 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
         dfree(ctx->d_types);
         CK(cudaMalloc(&ctx->d_accN, sizeof(double) * ctx->nlab * p->n_groups));
         CK(cudaMalloc(&ctx->d_accU, sizeof(double) * ctx->nlab * p->n_groups));
+        dfree(ctx->d_accA);
+        dfree(ctx->d_accB);
+        CK(cudaMalloc(&ctx->d_accA, sizeof(double) * ctx->nlab * p->n_groups));
+        CK(cudaMalloc(&ctx->d_accB, sizeof(double) * ctx->nlab * p->n_groups));
         CK(cudaMalloc(&ctx->d_accW, sizeof(double) * p->n_groups));
         CK(cudaMalloc(&ctx->d_accE, sizeof(double) * p->n_groups));
         CK(cudaMalloc(&ctx->d_types, sizeof(unsigned long long) * MRQ_NTYPES));
@@ -1813,6 +1871,8 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
     ctx->launches_total = 0;
     CK(cudaMemsetAsync(ctx->d_accN, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_accU, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_accA, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_accB, 0, sizeof(double) * ctx->nlab * ctx->G, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_accW, 0, sizeof(double) * ctx->G, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_accE, 0, sizeof(double) * ctx->G, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_types, 0, sizeof(unsigned long long) * MRQ_NTYPES, ctx->stream));
@@ -1921,6 +1981,55 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
                     "%d (use mrq_finalize)", (long long)ctx->nlab, ctx->G, need, MRQ_NOALLOC_SCRATCH_DOUBLES);
     CK(cudaSetDevice(ctx->device));
     return finalize_with(ctx, out, g_noalloc_ptr[ctx->device], nchunk);
+}
+
+int mrq_mrci_gradient(mrq_ctx* ctx, double* grad, double* energy) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref || !ctx->d_accA) return fail(ctx, MRQ_NOT_LOADED, "no walk to take the gradient from");
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->d_grad) CK(cudaMalloc(&ctx->d_grad, sizeof(double) * (ctx->nlab + 1)));
+    if (int r = push_sys(ctx)) return r;
+    k_mrci_grad<<<(unsigned)std::min<long long>(1024, (ctx->nlab + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_sys, ctx->d_grad, ctx->d_grad + ctx->nlab);
+    CK(cudaGetLastError());
+    double e = 0.0;
+    if (grad) CK(cudaMemcpyAsync(grad, ctx->d_grad, sizeof(double) * ctx->nlab, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(&e, ctx->d_grad + ctx->nlab, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (energy) *energy = e;
+    return 0;
+}
+
+int mrq_amsgrad_step(mrq_ctx* ctx, double lr, double beta1, double beta2, double eps) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->d_grad) return fail(ctx, MRQ_NOT_LOADED, "call mrq_mrci_gradient first");
+    if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+        return fail(ctx, MRQ_INVALID_ARG, "need lr > 0, 0 <= beta < 1, eps > 0");
+    CK(cudaSetDevice(ctx->device));
+    if (!ctx->d_am_m) {
+        CK(cudaMalloc(&ctx->d_am_m, sizeof(double) * ctx->nlab));
+        CK(cudaMalloc(&ctx->d_am_v, sizeof(double) * ctx->nlab));
+        CK(cudaMalloc(&ctx->d_am_vh, sizeof(double) * ctx->nlab));
+        CK(cudaMemsetAsync(ctx->d_am_m, 0, sizeof(double) * ctx->nlab, ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_am_v, 0, sizeof(double) * ctx->nlab, ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_am_vh, 0, sizeof(double) * ctx->nlab, ctx->stream));
+    }
+    k_amsgrad<<<(unsigned)std::min<long long>(1024, (ctx->nlab + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_c, ctx->d_grad, ctx->d_am_m, ctx->d_am_v, ctx->d_am_vh, ctx->nlab, lr, beta1, beta2, eps);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+int mrq_read_coeffs(mrq_ctx* ctx, double* c) {
+    if (!ctx || !c) return MRQ_INVALID_ARG;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(c, ctx->d_c, sizeof(double) * ctx->nlab, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
 }
 
 int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
@@ -2032,6 +2141,17 @@ int mrq_phase_times(unsigned long long* out8) {
     return 0;
 }
 #endif
+
+int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!ctx->d_accA) return fail(ctx, MRQ_NOT_LOADED, "no accumulators");
+    CK(cudaSetDevice(ctx->device));
+    const size_t bytes = sizeof(double) * ctx->nlab * ctx->G;
+    if (accA) CK(cudaMemcpyAsync(accA, ctx->d_accA, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (accB) CK(cudaMemcpyAsync(accB, ctx->d_accB, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
 
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
     if (!ctx) return MRQ_INVALID_ARG;

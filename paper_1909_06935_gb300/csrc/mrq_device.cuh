@@ -55,6 +55,8 @@ struct SysDev {
     double* accU;
     double* accW;
     double* accE;
+    double* accA;           // [G][nlab] sum w E_L / c_l      (SC-MRCI gradient, Eq. 8-9)
+    double* accB;           // [G][nlab] sum w / c_l
     unsigned long long* type_steps;
     int G;
     long long burn_in;
