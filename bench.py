@@ -355,20 +355,27 @@ def run_batched(args):
     params = [c.params(nw, 0, burn_in=0, seed=500 + k, n_groups=8) for k, (c, nw) in enumerate(zip(ctxs, walkers))]
     total = sum(walkers)
 
+    R = max(1, args.inner)      # walker steps per reporting interval (one finalize per system)
+
     def plain_step():
         for c in ctxs:
-            c.walkers_advance(1)
+            c.walkers_advance(R)
             c.finalize()
 
     def batched_step():
-        P.batch_advance(ctxs, 1)
+        P.batch_advance(ctxs, R)
         for c in ctxs:
             c.finalize()
 
-    out = {}
-    for name, fn in (("plain", plain_step), ("batched", batched_step)):
+    out, tune = {}, None
+    for name, fn in (("plain", plain_step), ("batched", batched_step), ("batched_tuned", batched_step)):
         for c, p in zip(ctxs, params):
             c.walkers_init(p)
+            c.set_launch()
+        if name == "batched_tuned":     # autotune walkers/block and steps/launch, then graph replay
+            tune = P.tune_batch(ctxs, trial_steps=min(R, 16))
+            for c in ctxs:
+                c.set_launch(tune["warps_per_block"], min(tune["steps_per_launch"], R), True)
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize(dev)
@@ -376,11 +383,16 @@ def run_batched(args):
         for _ in range(args.steps):
             fn()
         torch.cuda.synchronize(dev)
-        out[name] = total * args.steps / (time.perf_counter() - t0)
+        out[name] = total * R * args.steps / (time.perf_counter() - t0)
+    for c in ctxs:
+        c.set_launch()
     line = {"metric": METRIC, "mode": "batched", "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "plain": out["plain"], "batched": out["batched"],
-            "speedup": out["batched"] / out["plain"], "dtype": "f64", "data": "synthetic",
+            "batched_tuned": out["batched_tuned"], "speedup": out["batched"] / out["plain"],
+            "speedup_tuned": out["batched_tuned"] / out["plain"], "tuned_launch": tune,
+            "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batch{args.n_systems}", "systems": args.n_systems, "walkers": total,
+                       "steps_per_report": R,
                        "orbitals": [s.n_orb for s in systems], "reference_dets": [len(s.coeffs) for s in systems],
                        "generation_seconds": t_gen}}
     print(json.dumps(line), flush=True)

@@ -226,6 +226,37 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out);
  */
 int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps);
 
+/*
+ * Launch configuration of a context's walks (no counterpart in the paper: a GPU scheduling
+ * choice that leaves every trajectory and accumulator the same, up to the order of the FP64
+ * additions).  warps_per_block in {1, 2, 4} walkers per thread block (default 4);
+ * steps_per_launch >= 1 splits an advance into launches of that many steps, each re-ordering the
+ * walker slots first (0, the default: one launch per advance); use_graph != 0 makes
+ * mrq_batch_advance, with ctxs[0] this context, capture one launch of steps_per_launch steps (the
+ * reporting interval: slot sort + walk) into a CUDA graph once per batch layout and replay it.
+ * Errors: MRQ_INVALID_ARG.
+ */
+int mrq_set_launch(mrq_ctx* ctx, int warps_per_block, int steps_per_launch, int use_graph);
+
+#define MRQ_TUNE_MAX 16
+typedef struct {
+    int warps_per_block;      /* the fastest configuration, now set on every context of the batch */
+    int steps_per_launch;
+    int n_tried;
+    int tried_warps_per_block[MRQ_TUNE_MAX];
+    int tried_steps_per_launch[MRQ_TUNE_MAX];
+    double tried_ms[MRQ_TUNE_MAX];   /* device time of trial_steps steps, best of up to 3 */
+} mrq_tune_result;
+
+/*
+ * Autotuner of the batched walk: times trial_steps (1..1024) steps of the batch for every
+ * warps_per_block in {1, 2, 4} and steps_per_launch in {1, 4, 16} (those <= trial_steps), on a
+ * scratch copy of the walkers with accumulation off, so the contexts' walkers and accumulators
+ * are left as they were; then sets the fastest pair on every context (mrq_set_launch, keeping
+ * use_graph).  out may be NULL.  Errors: as mrq_batch_advance, MRQ_INVALID_ARG for trial_steps.
+ */
+int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_result* out);
+
 /* mrq_walkers_init for each context (params[i]), mrq_batch_advance(params[0].n_steps), and
  * mrq_finalize of each into out[i].  Every params[i].n_steps must be equal. */
 int mrq_sample_batch(mrq_ctx* const* ctxs, int n, const mrq_sample_params* params, mrq_result* out);

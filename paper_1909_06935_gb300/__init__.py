@@ -68,6 +68,21 @@ _LOCAL_DTYPE = np.dtype([("S", np.float64), ("e_local", np.float64), ("num", np.
 assert _NB_DTYPE.itemsize == C.sizeof(Neighbour) and _LOCAL_DTYPE.itemsize == C.sizeof(Local)
 
 
+TUNE_MAX = 16
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("steps_per_launch", C.c_int32), ("n_tried", C.c_int32),
+                ("tried_warps_per_block", C.c_int32 * TUNE_MAX), ("tried_steps_per_launch", C.c_int32 * TUNE_MAX),
+                ("tried_ms", C.c_double * TUNE_MAX)]
+
+    def as_dict(self):
+        n = self.n_tried
+        return dict(warps_per_block=self.warps_per_block, steps_per_launch=self.steps_per_launch,
+                    tried=[(self.tried_warps_per_block[i], self.tried_steps_per_launch[i], self.tried_ms[i])
+                           for i in range(n)])
+
+
 class MRQError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"mrq error {code}: {msg}")
@@ -110,6 +125,8 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_read_accumulators.argtypes = [P, P, P, P, P, P]
     lib.mrq_read_walkers.argtypes = [P, P, P]
     lib.mrq_batch_advance.argtypes = [P, C.c_int, I64]
+    lib.mrq_set_launch.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.mrq_tune_batch.argtypes = [P, C.c_int, I64, P]
     lib.mrq_mrci_gradient.argtypes = [P, P, P]
     lib.mrq_amsgrad_step.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double]
     lib.mrq_read_coeffs.argtypes = [P, P]
@@ -118,7 +135,8 @@ def load_library(build_if_missing: bool = True):
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
                "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch", "mrq_mrci_gradient",
-               "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_read_accumulators", "mrq_read_walkers"):
+               "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_set_launch",
+               "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -257,6 +275,11 @@ class Context:
         self._check(self._lib.mrq_read_accumulators(self._h, _addr(N), _addr(U), _addr(Wg), _addr(E), _addr(ts)))
         return dict(N=N, U=U, W=Wg, E=E, type_steps=ts)
 
+    def set_launch(self, warps_per_block=4, steps_per_launch=0, use_graph=False):
+        """Walk launch configuration: walkers per block, steps per launch (0 = one launch per
+        advance), CUDA-graph replay of batched reporting intervals."""
+        self._check(self._lib.mrq_set_launch(self._h, warps_per_block, steps_per_launch, int(bool(use_graph))))
+
     def mrci_gradient(self):
         """SC-MRCI(s) gradient (Eq. 8-9) of the last walk and the energy estimate."""
         g = np.zeros(self.n_labels)
@@ -311,6 +334,17 @@ def batch_advance(ctxs, n_steps: int):
     rc = lib.mrq_batch_advance(C.cast(_ctx_array(ctxs), C.c_void_p), len(ctxs), n_steps)
     if rc:
         raise MRQError(rc, lib.mrq_last_error(ctxs[0]._h).decode())
+
+
+def tune_batch(ctxs, trial_steps: int = 4):
+    """Autotune walkers per block and steps per launch for this batch (on scratch walkers; the
+    contexts' state is unchanged) and set the fastest on every context.  Returns the timings."""
+    lib = load_library()
+    out = TuneResult()
+    rc = lib.mrq_tune_batch(C.cast(_ctx_array(ctxs), C.c_void_p), len(ctxs), trial_steps, C.byref(out))
+    if rc:
+        raise MRQError(rc, lib.mrq_last_error(ctxs[0]._h).decode())
+    return out.as_dict()
 
 
 def sample_batch(ctxs, params):

@@ -506,10 +506,10 @@ __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, in
 // neighbouring warps, which then share cache lines (the results do not depend on the order).
 template <int W>
 __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet ws, int nsteps, int cap,
-                                                                   const unsigned* __restrict__ order) {
+                                                                   const unsigned* __restrict__ order, int accumulate) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const long long s0 = (long long)blockIdx.x * 4 + wi;
+    const long long s0 = (long long)blockIdx.x * (blockDim.x >> 5) + wi;
     if (s0 >= ws.nslots) return;
     const long long slot = order ? (long long)order[s0] : s0;
     int sys;
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet
             if (lane == 0) atomicOr(S.err, ln < 0 ? MRQ_ERR_LABEL : MRQ_ERR_NOMOVE);
             break;
         }
-        if (lane == 0 && (long long)wk.step >= S.burn_in) {
+        if (lane == 0 && accumulate && (long long)wk.step >= S.burn_in) {
             const double w = 1.0 / lo.S;
             const double cl = __ldg(S.c + ln);
             const double c2 = cl * cl;
@@ -1349,6 +1349,26 @@ struct mrq_ctx {
     SysDev hsys{};
     SysDev* d_sys = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch configuration (mrq_set_launch, mrq_tune_batch)
+    int wpb = 4;                     // walkers (warps) per block
+    int spl = 0;                     // steps per launch (0: every advance is one launch)
+    int use_graph = 0;               // batches replay one reporting interval from a CUDA graph
+    struct GraphKey {
+        const void *sys = nullptr, *wptr = nullptr, *off = nullptr, *keys = nullptr;
+        long long nslots = 0;
+        int k = 0, wpb = 0, spl = 0, cap = 0;
+        bool operator==(const GraphKey& o) const {
+            return sys == o.sys && wptr == o.wptr && off == o.off && keys == o.keys && nslots == o.nslots &&
+                   k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap;
+        }
+    };
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // per determinant width
+    GraphKey gkey[2];
+    long long graph_replays = 0;
+    Walker* d_tune = nullptr;        // the tuner's scratch copy of a batch's walkers
+    long long tune_cap = 0;
+    Walker** d_tptr = nullptr;
+    int tptr_cap = 0;
     std::vector<cudaEvent_t> evs;    // start/stop pairs of the walk launches since the last finalize
     int launches = 0;
     long long launches_total = 0;
@@ -1446,39 +1466,62 @@ static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
     return 0;
 }
 
+// launch-time options of a walk: warps (walkers) per block, whether to accumulate, and whether the
+// one-time set-up (buffer growth, function attributes) has been done already (inside a stream capture)
+struct WalkLaunch {
+    int wpb = 4;
+    int accumulate = 1;
+    bool captured = false;
+};
+
+static int walk_sort_prepare(mrq_ctx* ctx, long long nslots) {
+    if (nslots < 64 || nslots > MRQ_SORT_MAX) return 0;
+    long long npad = 1;
+    while (npad < nslots) npad <<= 1;
+    if (npad > ctx->sort_cap) {
+        dfree(ctx->d_sort_keys);
+        dfree(ctx->d_sort_idx);
+        CK(cudaMalloc(&ctx->d_sort_keys, sizeof(unsigned long long) * npad));
+        CK(cudaMalloc(&ctx->d_sort_idx, sizeof(unsigned) * npad));
+        ctx->sort_cap = npad;
+    }
+    const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
+    CK(cudaFuncSetAttribute(k_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    return 0;
+}
+
+static int walk_attr_prepare(mrq_ctx* ctx, int W, int wpb, int cap) {
+    const int smem = (int)(wpb * warp_smem_bytes(cap));
+    if (W == 1) CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    else CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return 0;
+}
+
 // walk launch: order the slots by determinant (when the slot count allows a one-block sort),
 // then one warp per slot; `ctx` provides the stream and the sort scratch
-static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int cap) {
-    const size_t smem = 4 * warp_smem_bytes(cap);
+static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int cap, const WalkLaunch& L = WalkLaunch()) {
+    const int wpb = L.wpb;
+    const size_t smem = wpb * warp_smem_bytes(cap);
     const unsigned* order = nullptr;
     const long long nslots = ws.nslots;
+    if (!L.captured) {
+        if (int r = walk_sort_prepare(ctx, nslots)) return r;
+        if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
+    }
     if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
         long long npad = 1;
         while (npad < nslots) npad <<= 1;
-        if (npad > ctx->sort_cap) {
-            dfree(ctx->d_sort_keys);
-            dfree(ctx->d_sort_idx);
-            CK(cudaMalloc(&ctx->d_sort_keys, sizeof(unsigned long long) * npad));
-            CK(cudaMalloc(&ctx->d_sort_idx, sizeof(unsigned) * npad));
-            ctx->sort_cap = npad;
-        }
         const unsigned nb = (unsigned)((npad + 255) / 256);
         if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
         else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
         const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
-        CK(cudaFuncSetAttribute(k_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
         k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
         CK(cudaGetLastError());
         order = ctx->d_sort_idx;
     }
-    const unsigned blocks = (unsigned)((nslots + 3) / 4);
-    if (W == 1) {
-        CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<1><<<blocks, 128, smem, ctx->stream>>>(ws, nsteps, cap, order);
-    } else {
-        CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_walk<2><<<blocks, 128, smem, ctx->stream>>>(ws, nsteps, cap, order);
-    }
+    const unsigned blocks = (unsigned)((nslots + wpb - 1) / wpb);
+    if (W == 1) k_walk<1><<<blocks, 32 * wpb, smem, ctx->stream>>>(ws, nsteps, cap, order, L.accumulate);
+    else k_walk<2><<<blocks, 32 * wpb, smem, ctx->stream>>>(ws, nsteps, cap, order, L.accumulate);
     CK(cudaGetLastError());
     return 0;
 }
@@ -1532,6 +1575,10 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_bsys);
     dfree(ctx->d_bwptr);
     dfree(ctx->d_boff);
+    dfree(ctx->d_tune);
+    dfree(ctx->d_tptr);
+    for (int w = 0; w < 2; w++)
+        if (ctx->gexec[w]) cudaGraphExecDestroy(ctx->gexec[w]);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1911,7 +1958,12 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
     WalkSet ws{ctx->d_sys, ctx->d_wptr, ctx->d_woff, 1, ctx->nwalk};
-    if (int r = launch_walk(ctx, ctx->W, ws, (int)n_steps, ctx->hsys.cand_cap)) return r;
+    WalkLaunch L;
+    L.wpb = ctx->wpb;
+    const int64_t spl = ctx->spl > 0 ? ctx->spl : n_steps;
+    for (int64_t done = 0; done < n_steps; done += spl)
+        if (int r = launch_walk(ctx, ctx->W, ws, (int)std::min<int64_t>(spl, n_steps - done), ctx->hsys.cand_cap, L))
+            return r;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
     ctx->launches++;
@@ -2032,7 +2084,7 @@ int mrq_read_coeffs(mrq_ctx* ctx, double* c) {
     return 0;
 }
 
-int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
+static int batch_check(mrq_ctx* const* ctxs, int n) {
     if (!ctxs || n <= 0) return MRQ_INVALID_ARG;
     mrq_ctx* lead = ctxs[0];
     if (!lead) return MRQ_INVALID_ARG;
@@ -2045,12 +2097,13 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
         for (int j = 0; j < i; j++)
             if (ctxs[j] == ctxs[i]) return fail(lead, MRQ_INVALID_ARG, "context %d appears twice", i);
     }
-    if (n_steps <= 0) return 0;
-    lead->err[0] = 0;
-    cudaError_t e0 = cudaSetDevice(lead->device);
-    if (e0 != cudaSuccess) return fail(lead, MRQ_CUDA_ERROR, "cudaSetDevice: %s", cudaGetErrorString(e0));
-    mrq_ctx* ctx = lead;   // for CK
-    for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
+    return 0;
+}
+
+// the batch's systems of determinant width W: device tables in the lead context, walker arrays
+// from `walkers` (the contexts' own, or the tuner's scratch copies)
+static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walkers, WalkSet& ws, int& cap) {
+    mrq_ctx* ctx = ctxs[0];
     if (n > ctx->bcap) {
         dfree(ctx->d_bsys);
         dfree(ctx->d_bwptr);
@@ -2060,24 +2113,98 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
         CK(cudaMalloc(&ctx->d_boff, sizeof(long long) * (n + 1)));
         ctx->bcap = n;
     }
-    // one launch per determinant width
-    for (int W = 1; W <= 2; W++) {
-        std::vector<SysDev> sys;
-        std::vector<Walker*> wp;
-        std::vector<long long> off(1, 0);
-        int cap = 1;
-        for (int i = 0; i < n; i++) {
-            if (ctxs[i]->W != W) continue;
-            sys.push_back(ctxs[i]->hsys);
-            wp.push_back(ctxs[i]->d_walk);
-            off.push_back(off.back() + ctxs[i]->nwalk);
-            cap = std::max(cap, ctxs[i]->hsys.cand_cap);
+    std::vector<SysDev> sys;
+    std::vector<Walker*> wp;
+    std::vector<long long> off(1, 0);
+    cap = 1;
+    for (int i = 0; i < n; i++) {
+        if (ctxs[i]->W != W) continue;
+        sys.push_back(ctxs[i]->hsys);
+        wp.push_back(walkers[i]);
+        off.push_back(off.back() + ctxs[i]->nwalk);
+        cap = std::max(cap, ctxs[i]->hsys.cand_cap);
+    }
+    ws = WalkSet{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, (int)sys.size(), off.back()};
+    if (sys.empty()) return 0;
+    const int k = (int)sys.size();
+    CK(cudaMemcpy(ctx->d_bsys, sys.data(), sizeof(SysDev) * k, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bwptr, wp.data(), sizeof(Walker*) * k, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_boff, off.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+// n_steps steps of one width's walk set: launches of `spl` steps (the reporting interval), each
+// one sort + one walk, replayed from a CUDA graph when the lead context asks for it
+static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int64_t n_steps, int wpb, int64_t spl,
+                     int accumulate, bool graph) {
+    WalkLaunch L;
+    L.wpb = wpb;
+    L.accumulate = accumulate;
+    if (spl <= 0 || spl > n_steps) spl = n_steps;
+    const int64_t nfull = n_steps / spl, rem = n_steps % spl;
+    if (graph && nfull > 0) {
+        if (int r = walk_sort_prepare(ctx, ws.nslots)) return r;
+        if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
+        mrq_ctx::GraphKey key;
+        key.sys = ws.systems;
+        key.wptr = ws.walkers;
+        key.off = ws.offsets;
+        key.keys = ctx->d_sort_keys;
+        key.nslots = ws.nslots;
+        key.k = ws.nsys;
+        key.wpb = wpb;
+        key.spl = (int)spl;
+        key.cap = cap;
+        cudaGraphExec_t& ex = ctx->gexec[W - 1];
+        if (!ex || !(ctx->gkey[W - 1] == key)) {
+            if (ex) CK(cudaGraphExecDestroy(ex));
+            ex = nullptr;
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            L.captured = true;
+            const int r = launch_walk(ctx, W, ws, (int)spl, cap, L);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (r || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return r ? r : fail(ctx, MRQ_CUDA_ERROR, "stream capture: %s", cudaGetErrorString(e));
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                ex = nullptr;
+                return fail(ctx, MRQ_CUDA_ERROR, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+            }
+            ctx->gkey[W - 1] = key;
         }
-        if (sys.empty()) continue;
-        const int k = (int)sys.size();
-        CK(cudaMemcpy(ctx->d_bsys, sys.data(), sizeof(SysDev) * k, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(ctx->d_bwptr, wp.data(), sizeof(Walker*) * k, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(ctx->d_boff, off.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice));
+        for (int64_t i = 0; i < nfull; i++) CK(cudaGraphLaunch(ex, ctx->stream));
+        ctx->graph_replays += nfull;
+        L.captured = false;
+    } else {
+        for (int64_t i = 0; i < nfull; i++)
+            if (int r = launch_walk(ctx, W, ws, (int)spl, cap, L)) return r;
+    }
+    if (rem > 0)
+        if (int r = launch_walk(ctx, W, ws, (int)rem, cap, L)) return r;
+    return 0;
+}
+
+int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
+    if (int r = batch_check(ctxs, n)) return r;
+    mrq_ctx* lead = ctxs[0];
+    if (n_steps <= 0) return 0;
+    lead->err[0] = 0;
+    cudaError_t e0 = cudaSetDevice(lead->device);
+    if (e0 != cudaSuccess) return fail(lead, MRQ_CUDA_ERROR, "cudaSetDevice: %s", cudaGetErrorString(e0));
+    mrq_ctx* ctx = lead;   // for CK
+    for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
+    std::vector<Walker*> own(n);
+    for (int i = 0; i < n; i++) own[i] = ctxs[i]->d_walk;
+    // one launch sequence per determinant width
+    for (int W = 1; W <= 2; W++) {
+        WalkSet ws;
+        int cap = 1;
+        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap)) return r;
+        if (ws.nsys == 0) continue;
         const size_t q = (size_t)ctx->launches * 2;
         while (ctx->evs.size() < q + 2) {
             cudaEvent_t ev;
@@ -2085,13 +2212,102 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
             ctx->evs.push_back(ev);
         }
         CK(cudaEventRecord(ctx->evs[q], ctx->stream));
-        WalkSet ws{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, k, off.back()};
-        if (int r = launch_walk(ctx, W, ws, (int)n_steps, cap)) return r;
+        if (int r = batch_run(ctx, W, ws, cap, n_steps, lead->wpb, lead->spl, 1, lead->use_graph != 0)) return r;
         CK(cudaEventRecord(ctx->evs[q + 1], ctx->stream));
         ctx->launches++;
         CK(cudaStreamSynchronize(ctx->stream));   // the tables are reused by the next width
     }
     for (int i = 0; i < n; i++) ctxs[i]->total_steps += n_steps * ctxs[i]->nwalk;
+    return 0;
+}
+
+int mrq_set_launch(mrq_ctx* ctx, int warps_per_block, int steps_per_launch, int use_graph) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4)
+        return fail(ctx, MRQ_INVALID_ARG, "warps_per_block must be 1, 2 or 4");
+    if (steps_per_launch < 0) return fail(ctx, MRQ_INVALID_ARG, "steps_per_launch must be >= 0");
+    ctx->wpb = warps_per_block;
+    ctx->spl = steps_per_launch;
+    ctx->use_graph = use_graph != 0;
+    return 0;
+}
+
+int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_result* out) {
+    if (int r = batch_check(ctxs, n)) return r;
+    mrq_ctx* ctx = ctxs[0];
+    if (trial_steps < 1 || trial_steps > 1024) return fail(ctx, MRQ_INVALID_ARG, "trial_steps must be in [1, 1024]");
+    ctx->err[0] = 0;
+    CK(cudaSetDevice(ctx->device));
+    for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
+    // scratch copies of every system's walkers: the trials move those, never the real ones
+    long long tot = 0;
+    for (int i = 0; i < n; i++) tot += ctxs[i]->nwalk;
+    if (tot > ctx->tune_cap) {
+        dfree(ctx->d_tune);
+        CK(cudaMalloc(&ctx->d_tune, sizeof(Walker) * tot));
+        ctx->tune_cap = tot;
+    }
+    std::vector<Walker*> scratch(n);
+    {
+        long long o = 0;
+        for (int i = 0; i < n; i++) {
+            scratch[i] = ctx->d_tune + o;
+            o += ctxs[i]->nwalk;
+        }
+    }
+    auto restore = [&]() -> int {
+        for (int i = 0; i < n; i++)
+            CK(cudaMemcpyAsync(scratch[i], ctxs[i]->d_walk, sizeof(Walker) * ctxs[i]->nwalk, cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+        return 0;
+    };
+    const int wpbs[3] = {1, 2, 4};
+    std::vector<int64_t> spls;
+    for (int64_t v : {(int64_t)1, (int64_t)4, (int64_t)16})
+        if (v <= trial_steps) spls.push_back(v);
+    mrq_tune_result res{};
+    double best = 1e300;
+    int reps = 3;
+    for (int pass = -1; pass < (int)(3 * spls.size()); pass++) {
+        const int wpb = pass < 0 ? 4 : wpbs[pass / (int)spls.size()];
+        const int64_t spl = pass < 0 ? 1 : spls[pass % spls.size()];
+        double ms_best = 1e300;
+        for (int rep = 0; rep < (pass < 0 ? 1 : reps); rep++) {
+            if (int r = restore()) return r;
+            CK(cudaEventRecord(ctx->ev0, ctx->stream));
+            for (int W = 1; W <= 2; W++) {
+                WalkSet ws;
+                int cap = 1;
+                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap)) return r;
+                if (ws.nsys == 0) continue;
+                if (int r = batch_run(ctx, W, ws, cap, trial_steps, wpb, spl, 0, false)) return r;
+                CK(cudaStreamSynchronize(ctx->stream));
+            }
+            CK(cudaEventRecord(ctx->ev1, ctx->stream));
+            CK(cudaEventSynchronize(ctx->ev1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+            ms_best = std::min(ms_best, (double)ms);
+            if (ms > 200.0f) reps = 1;     // long trials: one repetition is precise enough
+        }
+        if (pass < 0) continue;            // warm-up
+        if (res.n_tried < MRQ_TUNE_MAX) {
+            res.tried_warps_per_block[res.n_tried] = wpb;
+            res.tried_steps_per_launch[res.n_tried] = (int)spl;
+            res.tried_ms[res.n_tried] = ms_best;
+            res.n_tried++;
+        }
+        if (ms_best < best) {
+            best = ms_best;
+            res.warps_per_block = wpb;
+            res.steps_per_launch = (int)spl;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        ctxs[i]->wpb = res.warps_per_block;
+        ctxs[i]->spl = res.steps_per_launch;
+    }
+    if (out) *out = res;
     return 0;
 }
 

@@ -78,3 +78,71 @@ def test_batch_rejects_bad_lists():
     d = P.Context.from_system(s)               # no walkers yet
     with pytest.raises(P.MRQError):
         P.batch_advance([c, d], 1)
+
+
+def _run_batch(ctxs, walkers, seeds, steps, G, launch):
+    import paper_1909_06935_gb300 as P
+    for c in ctxs:
+        c.set_launch(*launch)
+    for c, nw, seed in zip(ctxs, walkers, seeds):
+        c.walkers_init(c.params(nw, steps, burn_in=2, seed=seed, n_groups=G))
+    P.batch_advance(ctxs, steps)
+    out = [(c.walkers(nw)[0], c.accumulators(G)) for c, nw in zip(ctxs, walkers)]
+    for c in ctxs:
+        c.set_launch()
+    return out
+
+
+@pytest.mark.parametrize("launch", [(1, 1, False), (2, 4, True), (4, 16, True), (1, 7, True), (2, 0, False)])
+def test_launch_configuration_leaves_results_unchanged(launch):
+    """Walkers per block, steps per launch (re-ordering the slots between launches) and CUDA-graph
+    replay change the schedule only: trajectories bit-identical, accumulators to rounding."""
+    import paper_1909_06935_gb300 as P
+    systems = _systems()
+    walkers, seeds, steps, G = [128, 64, 32, 96], [21, 22, 23, 24], 40, 4
+    ctxs = [P.Context.from_system(s) for s in systems]
+    ref = _run_batch(ctxs, walkers, seeds, steps, G, (4, 0, False))
+    got = _run_batch(ctxs, walkers, seeds, steps, G, launch)
+    got2 = _run_batch(ctxs, walkers, seeds, steps, G, launch)          # graph reuse
+    for k in range(len(systems)):
+        for g in (got, got2):
+            assert np.array_equal(ref[k][0], g[k][0]), (k, launch)
+            assert np.array_equal(ref[k][1]["type_steps"], g[k][1]["type_steps"])
+            for key in ("N", "U", "W", "E"):
+                assert _close(ref[k][1][key], g[k][1][key], 1e-12), (k, key)
+    for c in ctxs:
+        c.close()
+
+
+def test_tuner_leaves_state_unchanged_and_sets_a_tried_configuration():
+    import paper_1909_06935_gb300 as P
+    systems = _systems()
+    walkers, G = [128, 64, 32, 96], 4
+    ctxs = [P.Context.from_system(s) for s in systems]
+    for c, nw in zip(ctxs, walkers):
+        c.walkers_init(c.params(nw, 0, burn_in=0, seed=3, n_groups=G))
+    P.batch_advance(ctxs, 5)
+    before = [(c.walkers(nw)[0], c.accumulators(G)) for c, nw in zip(ctxs, walkers)]
+    t = P.tune_batch(ctxs, trial_steps=16)
+    assert len(t["tried"]) == 9 and all(ms > 0 for _, _, ms in t["tried"])
+    assert (t["warps_per_block"], t["steps_per_launch"]) in [(w, s) for w, s, _ in t["tried"]]
+    after = [(c.walkers(nw)[0], c.accumulators(G)) for c, nw in zip(ctxs, walkers)]
+    for (da, aa), (db, ab) in zip(before, after):
+        assert np.array_equal(da, db)
+        for key in ("N", "U", "W", "E", "type_steps"):
+            assert np.array_equal(aa[key], ab[key])
+    # the tuned configuration continues the same trajectories
+    for c in ctxs:
+        c.set_launch(t["warps_per_block"], t["steps_per_launch"], True)
+    P.batch_advance(ctxs, 10)
+    tuned = [c.walkers(nw)[0] for c, nw in zip(ctxs, walkers)]
+    for c, nw in zip(ctxs, walkers):
+        c.set_launch()
+        c.walkers_init(c.params(nw, 0, burn_in=0, seed=3, n_groups=G))
+    P.batch_advance(ctxs, 15)
+    for x, c, nw in zip(tuned, ctxs, walkers):
+        assert np.array_equal(x, c.walkers(nw)[0])
+    with pytest.raises(P.MRQError):
+        P.tune_batch(ctxs, trial_steps=0)
+    for c in ctxs:
+        c.close()
