@@ -44,6 +44,8 @@ typedef struct {
     int64_t nref;
     det_t *ref;           /* sorted */
     double *refc;
+    int64_t *hidx;        /* open-addressing index of ref: slot -> position + 1 (0 = empty) */
+    uint64_t hmask;
     double *c;            /* per label sampling coefficients */
     int64_t nlab;
     int64_t nHs, nPs;     /* numbers of hole sets and particle sets */
@@ -132,15 +134,23 @@ static int64_t det_label(const osys *S, const det_t *d, int *h_out, int *p_out) 
 
 /* ------------------------------------------------------------------ reference lookup */
 
+static uint64_t det_hash(const det_t *d) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    for (int s = 0; s < 2; s++)
+        for (int w = 0; w < 2; w++) {
+            h ^= d->w[s][w] + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+            h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
+        }
+    return h;
+}
+
+/* phi0(d): the reference coefficient of d, or 0 (hash index over the sorted list) */
 static double phi0(const osys *S, const det_t *d) {
-    int64_t lo = 0, hi = S->nref - 1;
-    while (lo <= hi) {
-        int64_t mid = (lo + hi) / 2;
-        int c = det_cmp(&S->ref[mid], d);
-        if (c == 0) return S->refc[mid];
-        if (c < 0) lo = mid + 1; else hi = mid - 1;
+    for (uint64_t i = det_hash(d) & S->hmask;; i = (i + 1) & S->hmask) {
+        int64_t k = S->hidx[i];
+        if (k == 0) return 0.0;
+        if (det_cmp(&S->ref[k - 1], d) == 0) return S->refc[k - 1];
     }
-    return 0.0;
 }
 
 /* ------------------------------------------------------------------ Slater-Condon (H) */
@@ -375,11 +385,21 @@ static void local_eval(const osys *S, const det_t *d, int do_move, uint64_t seed
     L->psi_n = psi_s(S, d, &on);
     L->Hnn = h_diag(S, d);
     L->HDnn = (L->label >= 0) ? hd_diag(S, d) : 0.0;
-    double sumH = 0.0, sumHD = 0.0, best = INFINITY;
+    double sumH = 0.0, sumHD = 0.0, Ssum = 0.0, best = INFINITY;
+    int64_t nnb = 0, terms = 0, rec = 0;     /* rec: neighbours recorded (serial when recording) */
     int occl[2 * MAXN], empl[2 * MAXN], no = 0, ne = 0;
     for (int so = 0; so < 2 * n; so++) { if (occ(d, so, n)) occl[no++] = so; else empl[ne++] = so; }
+    /* without a neighbour list the sums may run in parallel over the first removed electron (the
+     * sums then add in another order; the race winner is the same: smallest clock, then id) */
+    const int par = (nb_dets == NULL);
     for (int kind = 1; kind <= 2; kind++) {
-        for (int x1 = 0; x1 < no; x1++)
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) if (par) reduction(+ : sumH, sumHD, Ssum, nnb, terms)
+#endif
+        for (int x1 = 0; x1 < no; x1++) {
+            double tbest = INFINITY, tpsi = 0.0;
+            uint32_t tid = 0;
+            det_t tnext = *d;
             for (int x2 = (kind == 1 ? x1 : x1 + 1); x2 < (kind == 1 ? x1 + 1 : no); x2++)
                 for (int y1 = 0; y1 < ne; y1++)
                     for (int y2 = (kind == 1 ? y1 : y1 + 1); y2 < (kind == 1 ? y1 + 1 : ne); y2++) {
@@ -392,17 +412,17 @@ static void local_eval(const osys *S, const det_t *d, int do_move, uint64_t seed
                         if (kind == 2) { clrb(&m, r2, n); setb(&m, a2, n); }
                         int64_t lm = det_label(S, &m, NULL, NULL);
                         if (lm < 0) continue;
-                        double o, ps = psi_s_t(S, &m, &o, &L->terms);
+                        double o, ps = psi_s_t(S, &m, &o, &terms);
                         double hnm = h_elem(S, d, &m);
                         double hd = (L->label > 0 && lm == L->label) ? hd_elem(S, d, &m) : 0.0;
                         double ratio = (L->psi_n != 0.0) ? ps / L->psi_n : 0.0;
                         double gam = fabs(hnm * ratio);
                         sumH += hnm * ratio;
                         sumHD += hd * ratio;
-                        L->S += gam;
+                        Ssum += gam;
                         uint32_t id = exc_id(r1, r2, a1, a2);
-                        if (nb_dets && L->nnb < max_nb) {
-                            int64_t k = L->nnb;
+                        if (nb_dets && rec < max_nb) {
+                            int64_t k = rec++;
                             det_to_words(S, &m, nb_dets + k * 2 * S->W);
                             nb_vals[k * 5 + 0] = hnm;
                             nb_vals[k * 5 + 1] = hd;
@@ -411,15 +431,29 @@ static void local_eval(const osys *S, const det_t *d, int do_move, uint64_t seed
                             nb_vals[k * 5 + 4] = gam;
                             nb_exc[k] = id;
                         }
-                        L->nnb++;
+                        nnb++;
                         if (do_move && gam > 0.0) {
                             double t = race_clock(seed, id, step, walker, gam);
-                            if (t < best || (t == best && id < L->next_exc)) {
-                                best = t; L->next = m; L->next_psi = ps; L->next_exc = id;
+                            if (t < tbest || (t == tbest && id < tid)) {
+                                tbest = t; tnext = m; tpsi = ps; tid = id;
                             }
                         }
                     }
+            if (tbest < INFINITY) {
+#ifdef _OPENMP
+#pragma omp critical(oracle_race)
+#endif
+                {
+                    if (tbest < best || (tbest == best && tid < L->next_exc)) {
+                        best = tbest; L->next = tnext; L->next_psi = tpsi; L->next_exc = tid;
+                    }
+                }
+            }
+        }
     }
+    L->S = Ssum;
+    L->nnb = nnb;
+    L->terms = terms;
     L->EL = L->Hnn + sumH;
     L->num = (L->label > 0) ? L->HDnn + sumHD : 0.0;
 }
@@ -430,34 +464,45 @@ static int setup(osys *S) {
     int n = S->n, nc = S->nc, na = S->na;
     /* largest |phi0| determinant in input order was recorded by the caller */
     double norm = 0.0, num = 0.0;
-    S->gamma = calloc((size_t)(na > 0 ? na * na : 1), sizeof(double));
+    int nn = na > 0 ? na * na : 1;
+    double *g = calloc((size_t)nn, sizeof(double));
+    S->gamma = g;
+    /* active spin orbitals: the only ones a CAS-internal excitation touches */
+    int act[2 * MAXN], nact = 0;
+    for (int so = 0; so < 2 * n; so++)
+        if (orb_class(S, so % n) == 1) act[nact++] = so;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : norm, num) reduction(+ : g[:nn])
+#endif
     for (int64_t k = 0; k < S->nref; k++) {
         const det_t *d = &S->ref[k];
         double ck = S->refc[k];
         norm += ck * ck;
         num += ck * ck * h_diag(S, d);
-        for (int so = 0; so < 2 * n; so++)
-            if (orb_class(S, so % n) == 1 && occ(d, so, n)) S->gamma[(so % n - nc) * na + (so % n - nc)] += ck * ck;
+        for (int x = 0; x < nact; x++)
+            if (occ(d, act[x], n)) g[(act[x] % n - nc) * na + (act[x] % n - nc)] += ck * ck;
         /* active singles and doubles of d that stay in the CAS */
-        for (int r1 = 0; r1 < 2 * n; r1++) {
-            if (orb_class(S, r1 % n) != 1 || !occ(d, r1, n)) continue;
-            for (int a1 = 0; a1 < 2 * n; a1++) {
-                if (orb_class(S, a1 % n) != 1 || occ(d, a1, n) || a1 / n != r1 / n) continue;
+        for (int x1 = 0; x1 < nact; x1++) {
+            int r1 = act[x1];
+            if (!occ(d, r1, n)) continue;
+            for (int y1 = 0; y1 < nact; y1++) {
+                int a1 = act[y1];
+                if (occ(d, a1, n) || a1 / n != r1 / n) continue;
                 det_t m = *d; clrb(&m, r1, n); setb(&m, a1, n);
                 double cm = phi0(S, &m);
                 if (cm == 0.0) continue;
                 num += ck * h_elem(S, d, &m) * cm;
                 /* gamma_{a r} += <m| a+_a a_r |d> c_m c_d */
-                S->gamma[(a1 % n - nc) * na + (r1 % n - nc)] += single_sign(S, d, r1, a1) * cm * ck;
+                g[(a1 % n - nc) * na + (r1 % n - nc)] += single_sign(S, d, r1, a1) * cm * ck;
             }
         }
-        for (int r1 = 0; r1 < 2 * n; r1++)
-            for (int r2 = r1 + 1; r2 < 2 * n; r2++) {
-                if (orb_class(S, r1 % n) != 1 || orb_class(S, r2 % n) != 1) continue;
+        for (int x1 = 0; x1 < nact; x1++)
+            for (int x2 = x1 + 1; x2 < nact; x2++) {
+                int r1 = act[x1], r2 = act[x2];
                 if (!occ(d, r1, n) || !occ(d, r2, n)) continue;
-                for (int a1 = 0; a1 < 2 * n; a1++)
-                    for (int a2 = a1 + 1; a2 < 2 * n; a2++) {
-                        if (orb_class(S, a1 % n) != 1 || orb_class(S, a2 % n) != 1) continue;
+                for (int y1 = 0; y1 < nact; y1++)
+                    for (int y2 = y1 + 1; y2 < nact; y2++) {
+                        int a1 = act[y1], a2 = act[y2];
                         if (occ(d, a1, n) || occ(d, a2, n)) continue;
                         if ((r1 / n == 0) + (r2 / n == 0) != (a1 / n == 0) + (a2 / n == 0)) continue;
                         det_t m = *d;
@@ -505,7 +550,7 @@ void oracle_free(void *h) {
     osys *S = (osys *)h;
     if (!S) return;
     free(S->h1); free(S->eri); free(S->ref); free(S->refc); free(S->c);
-    free(S->gamma); free(S->heff); free(S->eps);
+    free(S->gamma); free(S->heff); free(S->eps); free(S->hidx);
     free(S);
 }
 
@@ -556,6 +601,15 @@ void *oracle_create(int nc, int na, int nv, int nalpha, int nbeta, const double 
         if (det_cmp(&S->ref[k - 1], &S->ref[k]) == 0) *status = -3;   /* duplicate determinant */
     free(arr); free(tmp); free(ord);
     if (*status) { oracle_free(S); return NULL; }
+    uint64_t cap = 1;
+    while (cap < 2 * (uint64_t)nref) cap <<= 1;
+    S->hmask = cap - 1;
+    S->hidx = calloc(cap, sizeof(int64_t));
+    for (int64_t k = 0; k < nref; k++) {
+        uint64_t i = det_hash(&S->ref[k]) & S->hmask;
+        while (S->hidx[i]) i = (i + 1) & S->hmask;
+        S->hidx[i] = k + 1;
+    }
     setup(S);
     return S;
 }

@@ -617,7 +617,7 @@ __global__ void k_walker_keys(const WalkSet ws, long long npad, unsigned long lo
 }
 
 // one-block bitonic sort of (key, index) pairs in shared memory, npad a power of two <= MRQ_SORT_MAX
-#define MRQ_SORT_MAX 8192
+#define MRQ_SORT_MAX 16384
 __global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict__ keys, unsigned* __restrict__ idx,
                                                   int npad) {
     extern __shared__ __align__(16) unsigned char sort_smem[];

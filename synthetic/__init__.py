@@ -4,7 +4,8 @@ This module stands in for the programs that produce the method's inputs in the p
 (the integral program and the CASSCF / selected-CI solver of the Results section):
 
 * one-electron integrals h1 and Cholesky-built two-electron integrals (pq|rs),
-* an exact CAS-CI ground state of the active space (the reference phi0),
+* an exact CAS-CI ground state of the active space, or a selected-CI vector for large active
+  spaces (the reference phi0),
 * core/virtual orbitals made semicanonical (the paper's H_D uses orbitals that
   diagonalise the core and virtual generalised Fock blocks, Sec. II C),
 * the random perturber coefficients c_l of the sampling function (Eq. 17).
@@ -24,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "System", "make_system", "workload", "pack_eri", "unpack_eri", "n_labels",
-    "psi_s_coeffs", "cas_strings", "casci", "WORKLOADS",
+    "psi_s_coeffs", "cas_strings", "casci", "sci", "make_sci_system", "WORKLOADS",
 ]
 
 
@@ -106,9 +107,10 @@ def cas_strings(norb: int, nel: int) -> np.ndarray:
                     dtype=np.int64)
 
 
-def _replacement_tables(strs: np.ndarray, norb: int):
+def _replacement_tables(strs: np.ndarray, norb: int, restrict: bool = False):
     """E_tu = a+_t a_u on a string space: {(t,u): (src, dst, sign)}; sign from the
-    number of occupied orbitals the operators pass (orbitals ordered ascending)."""
+    number of occupied orbitals the operators pass (orbitals ordered ascending).  With
+    restrict, replacements leading out of the given strings are dropped (P E_tu P)."""
     index = {int(s): i for i, s in enumerate(strs)}
     tabs = {}
     for t in range(norb):
@@ -124,6 +126,8 @@ def _replacement_tables(strs: np.ndarray, norb: int):
                     continue
                 ph += bin(s1 & ((1 << t) - 1)).count("1")
                 s2 = s1 | (1 << t)
+                if restrict and s2 not in index:
+                    continue
                 src.append(I)
                 dst.append(index[s2])
                 sgn.append(-1.0 if ph & 1 else 1.0)
@@ -281,6 +285,141 @@ def casci(h1, L, n_core, n_act, na, nb, e_nuc=0.0):
     return e, C, s.sa, s.sb, s.rdm1(C)
 
 
+# --------------------------------------------------------------------------- selected CI
+
+def _same_spin_hamiltonian(tabs, k, eri_a, nstr):
+    """Dense matrix of one spin's part of the active Hamiltonian on the full string space:
+    sum_tu k_tu E_tu + 1/2 sum_tuvw (tu|vw) E_tu E_vw (both operators of this spin)."""
+    n = k.shape[0]
+    Hs = np.zeros((nstr, nstr))
+    dmap = np.full((n * n, nstr), -1, dtype=np.int64)
+    smap = np.zeros((n * n, nstr))
+    for (t, u), (src, dst, sg) in tabs.items():
+        np.add.at(Hs, (dst, src), k[t, u] * sg)
+        dmap[t * n + u, src] = dst
+        smap[t * n + u, src] = sg
+    g = eri_a.reshape(n * n, n * n)
+    for (v, w), (src, dst, sg) in tabs.items():
+        if len(src) == 0:
+            continue
+        tgt = dmap[:, dst]                                   # (tu, m): E_tu applied after E_vw
+        val = 0.5 * g[:, v * n + w][:, None] * smap[:, dst] * sg[None, :]
+        ok = tgt >= 0
+        np.add.at(Hs, (tgt[ok], np.broadcast_to(src, tgt.shape)[ok]), val[ok])
+    return Hs
+
+
+class _ProductSpaceCI:
+    """CI in the product space S x S of selected alpha and beta strings (Sz = 0, n_alpha =
+    n_beta), with P H P applied exactly: same-spin parts as dense string-space matrices, the
+    opposite-spin part sum (tu|vw) E^a_tu E^b_vw through projected replacement tables."""
+
+    def __init__(self, e_core, heff, eri_a, strs_sel, Hs_sel):
+        self.n = n = heff.shape[0]
+        self.e_core = e_core
+        self.eri = eri_a
+        self.Hs = Hs_sel
+        self.tab = _replacement_tables(strs_sel, n, restrict=True)
+        self.m = m = len(strs_sel)
+        occ = np.array([[(int(x) >> t) & 1 for t in range(n)] for x in strs_sel], dtype=float)
+        J = np.einsum("ttuu->tu", eri_a)
+        hs = np.diag(Hs_sel)
+        self.diag = e_core + hs[:, None] + hs[None, :] + occ @ J @ occ.T
+        self.g = eri_a.reshape(n * n, n * n)
+        self.pairs = [(t, u) for t in range(n) for u in range(n)]
+
+    def sigma(self, C):
+        n, m = self.n, self.m
+        S = self.e_core * C + self.Hs @ C + C @ self.Hs.T
+        D = np.zeros((n * n, m, m))                        # D_vw = C (E^b_vw)^T
+        for i, (v, w) in enumerate(self.pairs):
+            src, dst, sg = self.tab[(v, w)]
+            if len(src):
+                D[i][:, dst] = C[:, src] * sg[None, :]
+        G = (self.g @ D.reshape(n * n, -1)).reshape(n * n, m, m)
+        for i, (t, u) in enumerate(self.pairs):            # sum_tu E^a_tu G_tu
+            src, dst, sg = self.tab[(t, u)]
+            if len(src):
+                S[dst] += sg[:, None] * G[i][src]
+        return S
+
+    def rdm1(self, C):
+        n = self.n
+        g = np.zeros((n, n))
+        nrm = np.vdot(C, C)
+        for (t, u), (src, dst, sg) in self.tab.items():
+            if len(src):
+                g[t, u] = (np.vdot(C[dst], sg[:, None] * C[src]) + np.vdot(C[:, dst], sg[None, :] * C[:, src])) / nrm
+        return g
+
+
+def sci(h1, L, n_core, n_act, n_el_spin, n_strings, n_seed_strings=256, e_nuc=0.0, tol=1e-5):
+    """Selected CI of the core-averaged active Hamiltonian (Sz = 0) by heat-bath selection of
+    strings: solve in the product space of the n_seed_strings strings of lowest same-spin
+    energy, score every other string s' by max_s |H_s's| sqrt(w_s) (w_s: the weight of string s
+    in that solution), keep the n_strings best, and solve again in their product space
+    (n_strings^2 determinants).  Returns (energy, C, strings, strings, gamma)."""
+    e_core, heff, eri_a = _active_hamiltonian(h1, L, n_core, n_act, e_nuc)
+    strs = cas_strings(n_act, n_el_spin)
+    k = heff - 0.5 * np.einsum("tvvu->tu", eri_a)
+    Hs = _same_spin_hamiltonian(_replacement_tables(strs, n_act), k, eri_a, len(strs))
+
+    def solve(sel, guess=None):
+        ci = _ProductSpaceCI(e_core, heff, eri_a, strs[sel], Hs[np.ix_(sel, sel)])
+        x0 = np.zeros((len(sel), len(sel)))
+        if guess is None:
+            x0.flat[np.argmin(ci.diag)] = 1.0
+        else:
+            x0 += guess
+        x0 += 1e-4 * np.random.Generator(np.random.PCG64(11)).normal(size=x0.shape)
+        e, C = _davidson(ci.sigma, ci.diag, x0, tol=tol, max_sub=24, max_iter=80)
+        return e, C, ci
+
+    seed_sel = np.sort(np.argsort(np.diag(Hs), kind="stable")[:min(n_seed_strings, len(strs))])
+    _, C0, _ = solve(seed_sel)
+    w = 0.5 * ((C0 ** 2).sum(1) + (C0 ** 2).sum(0))
+    score = (np.abs(Hs[:, seed_sel]) * np.sqrt(w)[None, :]).max(1)
+    score[seed_sel] = np.inf
+    sel = np.sort(np.argsort(-score, kind="stable")[:min(n_strings, len(strs))])
+    pos = np.searchsorted(sel, seed_sel)                 # the seed solution as the starting vector
+    guess = np.zeros((len(sel), len(sel)))
+    guess[np.ix_(pos, pos)] = C0
+    e, C, ci = solve(sel, guess)
+    if C.flat[np.argmax(np.abs(C))] < 0:
+        C = -C
+    return e, C, strs[sel], strs[sel], ci.rdm1(C)
+
+
+def _to_dets_fast(C, sa, sb, n_core, n_orb):
+    """_to_dets for a product space whose occupied orbitals all lie in the first word."""
+    W = (n_orb + 63) // 64
+    if n_core + max(int(sa.max()), int(sb.max())).bit_length() > 64:
+        raise ValueError("core and active orbitals must fit the first word")
+    core = np.uint64((1 << n_core) - 1)
+    ia, ib = np.indices(C.shape).reshape(2, -1)
+    dets = np.zeros((len(ia), 2 * W), dtype=np.uint64)
+    dets[:, 0] = core | (sa[ia].astype(np.uint64) << np.uint64(n_core))
+    dets[:, W] = core | (sb[ib].astype(np.uint64) << np.uint64(n_core))
+    return dets, C.ravel().astype(np.float64)
+
+
+def make_sci_system(n_core, n_act, n_virt, n_alpha, n_beta, rank, seed, n_strings, *, e_nuc=0.0,
+                    n_seed_strings=256, c_seed=None, **integral_kw) -> System:
+    """Integrals -> heat-bath selected-CI reference (n_strings^2 determinants) -> semicanonical
+    core/virtual -> packed inputs."""
+    if n_alpha != n_beta:
+        raise ValueError("the selected-CI generator builds Sz = 0 references")
+    h1, L = make_integrals(n_core, n_act, n_virt, rank, seed, **integral_kw)
+    e, C, sa, sb, gamma = sci(h1, L, n_core, n_act, n_alpha - n_core, n_strings, n_seed_strings, e_nuc)
+    h1, L = semicanonicalize(h1, L, n_core, n_act, gamma)
+    n = n_core + n_act + n_virt
+    dets, coeffs = _to_dets_fast(C, sa, sb, n_core, n)
+    nl = n_labels(n_core, n_virt)
+    c = psi_s_coeffs(nl, seed + 17 if c_seed is None else c_seed)
+    return System(n_core, n_act, n_virt, n_alpha, n_beta, np.ascontiguousarray(h1), pack_eri(L),
+                  e_nuc, dets, coeffs, float(e), c, meta=dict(rank=rank, seed=seed, gamma=gamma, L=L, sci=True))
+
+
 # --------------------------------------------------------------------------- semicanonical
 
 def _generalized_fock(h1, L, n_core, n_act, gamma):
@@ -408,6 +547,11 @@ WORKLOADS = {
     # reference = exact CAS(10e,10o) ground state (63,504 determinants)
     "cas10_56o": dict(n_core=6, n_act=10, n_virt=40, n_alpha=11, n_beta=11, rank=168, seed=2109,
                       chol_sigma=0.05),
+    # 104 spatial orbitals (10 core, 14 active, 80 virtual), 34 electrons (CAS(14e,14o)),
+    # Cholesky rank 312, factor scale 0.05, reference = heat-bath selected CI on the active
+    # Hamiltonian: the product space of 1,000 alpha x 1,000 beta strings (1,000,000 determinants)
+    "sci_104o_cas14": dict(n_core=10, n_act=14, n_virt=80, n_alpha=17, n_beta=17, rank=312, seed=2309,
+                           chol_sigma=0.05, n_strings=1000),
 }
 
 _CACHE: dict = {}
@@ -416,7 +560,8 @@ _CACHE: dict = {}
 def workload(name: str) -> System:
     """The named seeded workload (memoised in-process)."""
     if name not in _CACHE:
-        _CACHE[name] = make_system(**WORKLOADS[name])
+        spec = WORKLOADS[name]
+        _CACHE[name] = make_sci_system(**spec) if "n_strings" in spec else make_system(**spec)
     return _CACHE[name]
 
 

@@ -1,0 +1,102 @@
+"""104-orbital workload at full size: 10 core, 14 active, 80 virtual orbitals, 34 electrons, a
+1,000,000-determinant selected-CI reference (two words per spin; the hash table, labels and
+integral tables live in HBM).  Set-up, local quantities at CAS and FOIS determinants of every
+class type, and 16,384-walker trajectories against the oracle (the oracle's sums over the
+3.2 million neighbours of a CAS determinant run in parallel, so values agree to rounding)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def close(a, b, rtol=RTOL, atol=1e-13):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.all(np.abs(a - b) <= atol + rtol * np.maximum(np.abs(a), np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def c3():
+    import paper_1909_06935_gb300 as P
+    s = S.workload("sci_104o_cas14")
+    assert s.W == 2 and len(s.coeffs) == 1_000_000
+    return s, P.Context.from_system(s), O.Oracle.from_system(s)
+
+
+def _move(det, W, n, moves):
+    """Apply (spin, from, to) electron moves to a determinant (alpha words, then beta words)."""
+    d = det.copy()
+    for sg, p, q in moves:
+        for orb, on in ((p, False), (q, True)):
+            w, b = sg * W + orb // 64, np.uint64(1) << np.uint64(orb % 64)
+            assert bool(d[w] & b) != on, (sg, orb)
+            d[w] = (d[w] | b) if on else (d[w] & ~b)
+    return d
+
+
+def test_setup_parity(c3):
+    s, ctx, orc = c3
+    info = ctx.setup_info()
+    assert close(info["e0"], orc.e0, 1e-11)
+    assert close(info["norm0"], orc.norm0, 1e-11)
+    assert close(info["eps"], orc.eps, 1e-10)
+    assert close(info["gamma"], orc.gamma[:s.n_act, :s.n_act], 1e-10, 1e-12)
+    assert info["start"] == orc.start
+
+
+def test_local_quantities_every_class(c3):
+    s, ctx, orc = c3
+    n, W, nc, na = s.n_orb, s.W, s.n_core, s.n_act
+    start = s.dets[orc.start]
+
+    def occupied(sg, lo, hi):
+        return [p for p in range(lo, hi) if (int(start[sg * W + p // 64]) >> (p % 64)) & 1]
+
+    def empty(sg, lo, hi):
+        return [p for p in range(lo, hi) if not (int(start[sg * W + p // 64]) >> (p % 64)) & 1]
+
+    aocc, aemp = occupied(0, nc, nc + na), empty(0, nc, nc + na)
+    bocc, bemp = occupied(1, nc, nc + na), empty(1, nc, nc + na)
+    v0 = nc + na
+    dets = [start]
+    for moves in (
+        [(0, nc - 1, aemp[0])],                                  # (1,0)
+        [(1, bocc[0], v0 + 3)],                                  # (0,1)
+        [(0, 4, v0 + 50)],                                       # (1,1), virtual in word 1
+        [(0, nc - 2, aemp[0]), (1, nc - 1, bemp[1])],           # (2,0)
+        [(0, aocc[0], v0), (1, bocc[1], v0 + 41)],              # (0,2)
+        [(0, 3, v0 + 60), (1, 7, n - 1)],                        # (2,2), both virtuals in word 1
+        [(1, 2, v0 + 5), (1, bocc[2], v0 + 9)],                  # (1,2) same spin
+        [(0, 1, aemp[1]), (0, 6, v0 + 70)],                      # (2,1)
+    ):
+        dets.append(_move(start, W, n, moves))
+    dets = np.array(dets)
+    loc, _ = ctx.debug_local(dets)
+    types = []
+    for i, d in enumerate(dets):
+        r = orc.local(d)
+        types.append(r["type"])
+        assert loc["label"][i] == r["label"] and loc["type"][i] == r["type"]
+        assert loc["n_neighbours"][i] == r["nnb"] and loc["n_terms"][i] == r["terms"], i
+        for kg, ko in (("S", "S"), ("e_local", "EL"), ("num", "num"), ("h_nn", "Hnn"), ("hd_nn", "HDnn"),
+                       ("psi", "psi")):
+            assert close(loc[kg][i], r[ko]), (i, kg, loc[kg][i], r[ko])
+    assert sorted(types) == [0, 1, 2, 3, 4, 5, 6, 7, 8]
+
+
+def test_walk_16384_walkers_sampled_trajectories(c3):
+    s, ctx, orc = c3
+    nw, steps, seed = 16384, 2, 4711
+    ctx.walkers_init(ctx.params(nw, steps, burn_in=0, seed=seed, n_groups=16))
+    for _ in range(steps):
+        ctx.walkers_advance(1)
+    res = ctx.finalize()
+    assert res["status"] == 0 and res["walker_steps"] == nw * steps
+    dets, _ = ctx.walkers(nw)
+    for w in (0, nw - 1):
+        traj = orc.walk_one(w, steps, seed)
+        assert np.array_equal(dets[w], traj[-1]), w
