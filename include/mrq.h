@@ -67,8 +67,10 @@ typedef struct {
     int32_t n_groups;       /* G walker groups for jackknife errors (walker w is in group w mod G) */
     int32_t method;         /* mrq_method: informative; both estimators are always accumulated */
     double screen_tau;      /* perturbers with N_l/N_0 below this are screened out (Sec. II C) */
-    int32_t walkers_per_block; /* 0: library default */
-    int32_t reserved;
+    int32_t walkers_per_block; /* 1, 2 or 4 walkers per thread block; 0 keeps the context's setting */
+    int32_t steps_per_check;   /* mrq_sample with target_sigma: steps between error checks (0: n_steps/16) */
+    double target_sigma;    /* mrq_sample stops early once the jackknife sigma of E^(2) (method
+                               SC_NEVPT2) or of E (SC_MRCI) is at or below this; 0 = off */
 } mrq_sample_params;
 
 /* Result of a sampling run (all energies in Hartree). */
@@ -325,7 +327,10 @@ const char* mrq_server_last_error(const mrq_server* s);
 /* Stop, free every resident request, destroy. */
 void mrq_server_destroy(mrq_server* s);
 
-/* mrq_walkers_init + mrq_walkers_advance(p->n_steps) + mrq_finalize. */
+/* mrq_walkers_init + mrq_walkers_advance(p->n_steps) + mrq_finalize.  With p->target_sigma > 0
+ * the walk advances steps_per_check steps at a time and stops at the first check (after the
+ * burn-in) whose sigma is at or below the target, or after n_steps; out->total_steps says how far
+ * it went.  Errors: as the three calls. */
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out);
 
 /*

@@ -25,7 +25,7 @@ SC_NEVPT2, SC_MRCI = 0, 1
 class SampleParams(C.Structure):
     _fields_ = [("n_walkers", C.c_int64), ("n_steps", C.c_int64), ("burn_in", C.c_int64), ("seed", C.c_uint64),
                 ("n_groups", C.c_int32), ("method", C.c_int32), ("screen_tau", C.c_double),
-                ("walkers_per_block", C.c_int32), ("reserved", C.c_int32)]
+                ("walkers_per_block", C.c_int32), ("steps_per_check", C.c_int32), ("target_sigma", C.c_double)]
 
 
 class Result(C.Structure):
@@ -148,6 +148,19 @@ def n_labels(n_core: int, n_virt: int) -> int:
     return nh * npart
 
 
+def frozen_core_coeffs(c, n_core: int, n_virt: int):
+    """Sampling coefficients of the frozen-core variant (the paper's own implementation, Sec. II D):
+    c_l = 0 for every label with a core hole, so that psi_s vanishes on core-excited determinants,
+    walkers never reach them and only the (0,1) and (0,2) classes are sampled.  Label
+    l = rank(H) n_P + rank(P), so the labels with core holes are l >= n_P."""
+    c = np.array(c, dtype=np.float64, copy=True)
+    if len(c) != n_labels(n_core, n_virt):
+        raise ValueError("coefficient vector does not match the label count")
+    n_p = 1 + 2 * n_virt + (2 * n_virt) * (2 * n_virt - 1) // 2
+    c[n_p:] = 0.0
+    return c
+
+
 def _addr(a):
     """Address of a host numpy array or a CUDA torch tensor (unified addressing)."""
     if hasattr(a, "data_ptr"):
@@ -240,8 +253,10 @@ class Context:
                                               _addr(nb) if max_nb else None))
         return loc, (nb.reshape(n, max_nb) if max_nb else None)
 
-    def params(self, n_walkers, n_steps, burn_in=0, seed=1, n_groups=16, screen_tau=1e-10, method=SC_NEVPT2):
-        return SampleParams(n_walkers, n_steps, burn_in, seed, n_groups, method, screen_tau, 0, 0)
+    def params(self, n_walkers, n_steps, burn_in=0, seed=1, n_groups=16, screen_tau=1e-10, method=SC_NEVPT2,
+               walkers_per_block=0, target_sigma=0.0, steps_per_check=0):
+        return SampleParams(n_walkers, n_steps, burn_in, seed, n_groups, method, screen_tau, walkers_per_block,
+                            steps_per_check, target_sigma)
 
     def walkers_init(self, p: SampleParams):
         self._check(self._lib.mrq_walkers_init(self._h, C.byref(p)))
@@ -435,7 +450,7 @@ class Server:
         h1, eri, dets, co, cc = arrays
         req = Request(s.n_core, s.n_act, s.n_virt, s.n_alpha, s.n_beta, 0, float(s.e_nuc), _addr(h1).value,
                       _addr(eri).value, len(co), _addr(dets).value, _addr(co).value, len(cc), _addr(cc).value,
-                      SampleParams(n_walkers, 0, burn_in, seed, n_groups, 0, screen_tau, 0, 0),
+                      SampleParams(n_walkers, 0, burn_in, seed, n_groups, 0, screen_tau, 0, 0, 0.0),
                       float(target_sigma), int(max_steps))
         t = C.c_int64(0)
         rc = self._lib.mrq_server_submit(self._h, C.byref(req), C.byref(t))

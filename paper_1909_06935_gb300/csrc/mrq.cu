@@ -1883,6 +1883,11 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
     if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
     if (p->n_walkers <= 0 || p->n_groups <= 0 || p->n_groups > 64 || p->n_steps < 0 || p->burn_in < 0)
         return fail(ctx, MRQ_INVALID_ARG, "need n_walkers > 0, 1 <= n_groups <= 64, n_steps >= 0, burn_in >= 0");
+    if (p->walkers_per_block != 0 && p->walkers_per_block != 1 && p->walkers_per_block != 2 && p->walkers_per_block != 4)
+        return fail(ctx, MRQ_INVALID_ARG, "walkers_per_block must be 0, 1, 2 or 4");
+    if (p->steps_per_check < 0 || p->target_sigma < 0.0)
+        return fail(ctx, MRQ_INVALID_ARG, "need steps_per_check >= 0 and target_sigma >= 0");
+    if (p->walkers_per_block) ctx->wpb = p->walkers_per_block;
     CK(cudaSetDevice(ctx->device));
     if (p->n_walkers > ctx->walk_cap) {
         dfree(ctx->d_walk);
@@ -2329,8 +2334,25 @@ int mrq_sample_batch(mrq_ctx* const* ctxs, int n, const mrq_sample_params* param
 
 int mrq_sample(mrq_ctx* ctx, const mrq_sample_params* p, mrq_result* out) {
     if (int r = mrq_walkers_init(ctx, p)) return r;
-    if (int r = mrq_walkers_advance(ctx, p->n_steps)) return r;
-    return mrq_finalize(ctx, out);
+    if (!(p->target_sigma > 0.0)) {
+        if (int r = mrq_walkers_advance(ctx, p->n_steps)) return r;
+        return mrq_finalize(ctx, out);
+    }
+    const int64_t chunk = p->steps_per_check > 0 ? p->steps_per_check : std::max<int64_t>(1, p->n_steps / 16);
+    int64_t done = 0;
+    bool fresh = false;
+    while (done < p->n_steps) {
+        const int64_t k = std::min(chunk, p->n_steps - done);
+        if (int r = mrq_walkers_advance(ctx, k)) return r;
+        done += k;
+        fresh = false;
+        if (done <= p->burn_in) continue;
+        if (int r = mrq_finalize(ctx, out)) return r;
+        fresh = true;
+        const double sig = p->method == MRQ_SC_MRCI ? out->e_var_sigma : out->e2_sigma;
+        if (sig <= p->target_sigma) break;
+    }
+    return fresh ? 0 : mrq_finalize(ctx, out);
 }
 
 int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW, double* accE, int64_t* type_steps) {

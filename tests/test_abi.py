@@ -33,7 +33,7 @@ def test_struct_layouts_match_header_sizes():
     # mrq_neighbour: 4 words + 5 doubles + 2 uint32 = 80 bytes; mrq_local: 6 doubles + 7 int64 = 104
     assert ctypes.sizeof(P.Neighbour) == 80
     assert ctypes.sizeof(P.Local) == 104
-    assert ctypes.sizeof(P.SampleParams) == 56
+    assert ctypes.sizeof(P.SampleParams) == 64
 
 
 def test_label_count_matches_generator():

@@ -208,3 +208,33 @@ def test_full_size_launch_sampled_walkers_and_dets():
     for key_g, key_o in (("S", "S"), ("e_local", "EL"), ("h_nn", "Hnn"), ("psi", "psi")):
         assert close(loc[key_g][0], r[key_o]), key_g
     assert loc["n_neighbours"][0] == r["nnb"] and loc["n_terms"][0] == r["terms"]
+
+
+def test_target_sigma_stops_early_and_equals_a_fixed_length_run(tiny_pair):
+    s, ctx, orc = tiny_pair
+    ctx.set_coeffs(s.c)
+    p = ctx.params(512, 4000, burn_in=20, seed=31, n_groups=16, target_sigma=2e-3, steps_per_check=40)
+    res = ctx.sample(p)
+    steps = res["total_steps"] // 512
+    assert res["e2_sigma"] <= 2e-3 and steps < 4000 and steps % 40 == 0
+    ref = ctx.sample(ctx.params(512, steps, burn_in=20, seed=31, n_groups=16, walkers_per_block=2))
+    for k in ("e2", "e2_sigma", "e_var", "a0sq"):
+        assert close(res[k], ref[k], 1e-9), k
+    ctx.walkers_init(ctx.params(32, 0, walkers_per_block=4))
+
+
+def test_frozen_core_variant_within_3_sigma_of_brute_force(tiny_pair):
+    """c_l = 0 on core-hole labels: only the (0,1) and (0,2) classes are sampled, and E^(2) hits the
+    brute-force sum over the core-free labels."""
+    import paper_1909_06935_gb300 as P
+    s, ctx, orc = tiny_pair
+    types = O.label_types(s.n_core, s.n_virt)
+    ex = O.exact_from_brute(orc.brute(), orc.e0, orc.c, s.n_core, s.n_virt)
+    e2_frozen = ex["type_e2"][:3].sum()                 # types 3h + p with h = 0
+    ctx.set_coeffs(P.frozen_core_coeffs(s.c, s.n_core, s.n_virt))
+    try:
+        res = ctx.sample(ctx.params(2048, 800, burn_in=100, seed=78, n_groups=32))
+    finally:
+        ctx.set_coeffs(s.c)
+    assert np.all(res["type_steps"][3:] == 0) and np.all(res["type_e2"][3:] == 0)
+    assert abs(res["e2"] - e2_frozen) < 3 * res["e2_sigma"]

@@ -346,3 +346,24 @@ def test_walk_matches_exact_expectations():
     occ = acc["N"].sum(0) * o.c ** 2 / W
     big = ex["rho_label"] > 1e-3
     np.testing.assert_allclose(occ[big], ex["rho_label"][big], rtol=0.15)
+
+
+def test_frozen_core_variant_is_the_core_free_part_of_the_sum():
+    """Zero coefficients on core-hole labels (the paper's frozen-core implementation): the walk never
+    visits a core-excited class, and E^(2) is the brute-force sum over the core-free labels, which
+    equals the brute force restricted to those labels (N_l and E_l do not depend on c)."""
+    import paper_1909_06935_gb300 as P
+    s = tiny(1, 2, 2, 2, 2, seed=31)
+    types = O.label_types(1, 2)
+    cf = np.where(types >= 3, 0.0, s.c)
+    assert np.array_equal(P.frozen_core_coeffs(s.c, 1, 2), cf)     # the binding's helper (plain numpy)
+    o = O.Oracle.from_system(s)
+    of = O.Oracle.from_system(s, c=cf)
+    full = O.exact_from_brute(o.brute(), o.e0, o.c, 1, 2)
+    e2_frozen = full["type_e2"][:3].sum()          # types 3h + p with h = 0
+    acc = of.sample(64, 1500, 100, seed=5, n_groups=16)
+    assert np.all(acc["type_steps"][3:] == 0)
+    f = of.finalize(acc)
+    assert np.all(f["type_e2"][3:] == 0)
+    assert abs(f["e2"] - e2_frozen) < 4 * f["e2_sigma"]
+    assert abs(f["e2"] - full["e2"]) > 4 * f["e2_sigma"]          # core correlation is not small here
