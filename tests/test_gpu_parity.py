@@ -228,7 +228,6 @@ def test_frozen_core_variant_within_3_sigma_of_brute_force(tiny_pair):
     brute-force sum over the core-free labels."""
     import paper_1909_06935_gb300 as P
     s, ctx, orc = tiny_pair
-    types = O.label_types(s.n_core, s.n_virt)
     ex = O.exact_from_brute(orc.brute(), orc.e0, orc.c, s.n_core, s.n_virt)
     e2_frozen = ex["type_e2"][:3].sum()                 # types 3h + p with h = 0
     ctx.set_coeffs(P.frozen_core_coeffs(s.c, s.n_core, s.n_virt))
