@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--system", default=WORKLOAD, help="named synthetic workload of the plain path")
     ap.add_argument("--inner", type=int, default=1, help="walker steps per walk launch")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,7 +171,7 @@ def run_reference(args):
         return
     import oracle as O
     import synthetic as S
-    system = S.workload(WORKLOAD)
+    system = S.workload(args.system)
     threads = os.cpu_count() or 1
     orc = O.Oracle.from_system(system)
     per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
@@ -185,7 +186,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * meta["walkers"] * meta["steps"] / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "walkers_per_step": meta["walkers"], "steps_per_walker": meta["steps"]},
+        "config": {"workload": args.system, "walkers_per_step": meta["walkers"], "steps_per_walker": meta["steps"]},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
                          "sample": f"{meta['walkers']} walkers x {meta['steps']} steps per timed step"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -206,7 +207,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    system = S.workload(WORKLOAD)
+    system = S.workload(args.system)
     stream = torch.cuda.current_stream(dev)
     ctx = P.Context(local)
     ctx.set_stream(stream.cuda_stream)
@@ -318,7 +319,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "orbitals": "6 core, 10 active, 40 virtual", "electrons": 22,
+            "config": {"workload": args.system,
+                       "orbitals": f"{system.n_core} core, {system.n_act} active, {system.n_virt} virtual",
+                       "electrons": system.n_alpha + system.n_beta,
                        "reference_dets": int(len(system.coeffs)), "walkers_per_gpu": nw,
                        "walker_steps_per_launch": inner, "groups": 16, "method": "SC-NEVPT2(s) + E_L",
                        "l2": "256 MB buffer written between timed steps",
