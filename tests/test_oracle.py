@@ -367,3 +367,19 @@ def test_frozen_core_variant_is_the_core_free_part_of_the_sum():
     assert np.all(f["type_e2"][3:] == 0)
     assert abs(f["e2"] - e2_frozen) < 4 * f["e2_sigma"]
     assert abs(f["e2"] - full["e2"]) > 4 * f["e2_sigma"]          # core correlation is not small here
+
+
+def test_e2_does_not_depend_on_the_sampling_coefficients():
+    """The sampling coefficients c_l only shape |psi_s|^2 (Eq. 17): N_l, E_l and E^(2) are the same
+    for any choice, and walks with two different c vectors agree with that one value."""
+    base = tiny(1, 2, 2, 2, 2, seed=31, c_seed=101)
+    other = tiny(1, 2, 2, 2, 2, seed=31, c_seed=202)
+    assert not np.allclose(base.c, other.c)
+    oa, ob = O.Oracle.from_system(base), O.Oracle.from_system(other)
+    ba, bb = oa.brute(), ob.brute()
+    np.testing.assert_allclose(ba["N"], bb["N"], rtol=1e-12)
+    np.testing.assert_allclose(ba["D"], bb["D"], rtol=1e-12, atol=1e-14)
+    e2 = O.exact_from_brute(ba, oa.e0, oa.c, 1, 2)["e2"]
+    for o in (oa, ob):
+        f = o.finalize(o.sample(64, 1500, 100, seed=9, n_groups=16))
+        assert abs(f["e2"] - e2) < 4 * f["e2_sigma"]
