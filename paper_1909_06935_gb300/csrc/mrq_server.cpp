@@ -66,7 +66,7 @@ int64_t footprint_of(const Request& r) {
     const int64_t nca = r.n_core + r.n_act, nav = r.n_act + r.n_virt;
     b += 8 * (2 * n * n + neri + npair * n * n + 2 * nca * nca * nav * nav + n + r.n_act * r.n_act);
     b += 16 * cap + 8 * nlab;
-    b += 16 * G * nlab + 16 * G;
+    b += 32 * G * nlab + 16 * G;        // N, U and the SC-MRCI gradient sums A, B per group
     b += 64 * r.params.n_walkers + 16 * 8192;
     return b;
 }
