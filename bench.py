@@ -29,6 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "cas10_56o"
+# DRAM bytes (read + write) per walker-step of k_walk on the 56-orbital workload, from one ncu
+# capture of a steady-state 4,096-walker launch (23.05 MB); null for other workloads
+TRAFFIC_PER_WALKER_STEP = {"cas10_56o": 23.053056e6 / 4096}
 METRIC = "walker-steps/s"
 # FP64 FMA pipe of GB300: 2 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -269,7 +272,10 @@ def run_ours(args):
     achieved = flops_per_step * units_per_launch / launch_s / 1e12
     peaks, peak_kind = load_peaks()
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_walk",
+            "frac": achieved / fp64_peak,
+            "traffic": (TRAFFIC_PER_WALKER_STEP[args.system] * units_per_launch
+                        if args.system in TRAFFIC_PER_WALKER_STEP else None),
+            "kernel": "k_walk",
             "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (probe on this pool: 1.254 TFLOP/s)",
             "flops_per_walker_step": flops_per_step, "terms_per_walker_step": terms,
             "launch_seconds": launch_s, "launches_timed": int(walk_launches),
