@@ -488,6 +488,8 @@ struct WalkSet {
     const long long* offsets;
     int nsys;
     long long nslots;
+    double* gscr = nullptr;       // per slot: the CAS walker's single-excitation operator (gstride doubles)
+    long long gstride = 0;
 };
 
 __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, int& sys, long long& local) {
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet
         LocalOut lo;
         if (ln == 0)
             lo = local_eval_cas<W, MODE_STEP>(S, sh, cphi, ccode, n, psin, wk.step, wk.wid, lane, nxt, npsi, nexc,
-                                              nullptr, 0, nc);
+                                              nullptr, 0, nc, ws.gscr ? ws.gscr + s0 * ws.gstride : nullptr);
         else {
             PHASE_T0();
             lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc, nullptr,
@@ -656,7 +658,8 @@ __global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict
 template <int W>
 __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, const unsigned long long* __restrict__ dets,
                                                long long ndet, mrq_local* __restrict__ out, long long max_nb,
-                                               mrq_neighbour* __restrict__ nb, int cap) {
+                                               mrq_neighbour* __restrict__ nb, int cap, double* __restrict__ gscr,
+                                               long long gstride) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long i = (long long)blockIdx.x * 4 + wi;
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, c
     LocalOut lo;
     if (ln == 0 && psin != 0.0)
         lo = local_eval_cas<W, MODE_DEBUG>(S, sh, cphi, ccode, n, psin, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb,
-                                           ctr);
+                                           ctr, (gscr != nullptr && gstride > 0) ? gscr + i * gstride : nullptr);
     else
         lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb, ctr);
     unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands, ct = ctr.terms;
@@ -1354,17 +1357,19 @@ struct mrq_ctx {
     int spl = 0;                     // steps per launch (0: every advance is one launch)
     int use_graph = 0;               // batches replay one reporting interval from a CUDA graph
     struct GraphKey {
-        const void *sys = nullptr, *wptr = nullptr, *off = nullptr, *keys = nullptr;
+        const void *sys = nullptr, *wptr = nullptr, *off = nullptr, *keys = nullptr, *gscr = nullptr;
         long long nslots = 0;
         int k = 0, wpb = 0, spl = 0, cap = 0;
         bool operator==(const GraphKey& o) const {
-            return sys == o.sys && wptr == o.wptr && off == o.off && keys == o.keys && nslots == o.nslots &&
+            return sys == o.sys && wptr == o.wptr && off == o.off && keys == o.keys && gscr == o.gscr && nslots == o.nslots &&
                    k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap;
         }
     };
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // per determinant width
     GraphKey gkey[2];
     long long graph_replays = 0;
+    double* d_gscr = nullptr;        // per walk slot: a CAS walker's single-excitation operator
+    long long gscr_cap = 0;
     Walker* d_tune = nullptr;        // the tuner's scratch copy of a batch's walkers
     long long tune_cap = 0;
     Walker** d_tptr = nullptr;
@@ -1490,24 +1495,45 @@ static int walk_sort_prepare(mrq_ctx* ctx, long long nslots) {
     return 0;
 }
 
+#ifndef MRQ_WALK_CARVEOUT
+#define MRQ_WALK_CARVEOUT -1     // preferred shared-memory carveout of k_walk in percent (-1: driver default)
+#endif
+
+// the walk set's per-slot scratch of the CAS walkers' single-excitation operators
+static int walk_gscr_prepare(mrq_ctx* ctx, long long doubles) {
+    if (doubles > ctx->gscr_cap) {
+        dfree(ctx->d_gscr);
+        CK(cudaMalloc(&ctx->d_gscr, sizeof(double) * doubles));
+        ctx->gscr_cap = doubles;
+    }
+    return 0;
+}
+
 static int walk_attr_prepare(mrq_ctx* ctx, int W, int wpb, int cap) {
     const int smem = (int)(wpb * warp_smem_bytes(cap));
     if (W == 1) CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     else CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (MRQ_WALK_CARVEOUT >= 0) {
+        if (W == 1) CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributePreferredSharedMemoryCarveout, MRQ_WALK_CARVEOUT));
+        else CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributePreferredSharedMemoryCarveout, MRQ_WALK_CARVEOUT));
+    }
     return 0;
 }
 
 // walk launch: order the slots by determinant (when the slot count allows a one-block sort),
 // then one warp per slot; `ctx` provides the stream and the sort scratch
-static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int cap, const WalkLaunch& L = WalkLaunch()) {
+static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws_in, int nsteps, int cap, const WalkLaunch& L = WalkLaunch()) {
     const int wpb = L.wpb;
     const size_t smem = wpb * warp_smem_bytes(cap);
     const unsigned* order = nullptr;
-    const long long nslots = ws.nslots;
+    const long long nslots = ws_in.nslots;
     if (!L.captured) {
         if (int r = walk_sort_prepare(ctx, nslots)) return r;
         if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
+        if (int r = walk_gscr_prepare(ctx, nslots * ws_in.gstride)) return r;
     }
+    WalkSet ws = ws_in;
+    ws.gscr = ws.gstride > 0 ? ctx->d_gscr : nullptr;
     if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
         long long npad = 1;
         while (npad < nslots) npad <<= 1;
@@ -1577,6 +1603,7 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_boff);
     dfree(ctx->d_tune);
     dfree(ctx->d_tptr);
+    dfree(ctx->d_gscr);
     for (int w = 0; w < 2; w++)
         if (ctx->gexec[w]) cudaGraphExecDestroy(ctx->gexec[w]);
     for (auto e : ctx->evs) cudaEventDestroy(e);
@@ -1857,12 +1884,16 @@ int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* lo
     const unsigned blocks = (unsigned)((n + 3) / 4);
     const int cap = ctx->hsys.cand_cap;
     const size_t smem = 4 * warp_smem_bytes(cap);
+    const long long gstride = 2LL * ctx->hsys.nca * ctx->hsys.nav;
+    if (int r = walk_gscr_prepare(ctx, n * gstride)) return r;
     if (W == 1) {
         CK(cudaFuncSetAttribute(k_debug<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_debug<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap);
+        k_debug<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap, ctx->d_gscr,
+                                                       gstride);
     } else {
         CK(cudaFuncSetAttribute(k_debug<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_debug<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap);
+        k_debug<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap, ctx->d_gscr,
+                                                       gstride);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(local, d_loc, sizeof(mrq_local) * n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1963,6 +1994,7 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
     WalkSet ws{ctx->d_sys, ctx->d_wptr, ctx->d_woff, 1, ctx->nwalk};
+    ws.gstride = 2LL * ctx->hsys.nca * ctx->hsys.nav;
     WalkLaunch L;
     L.wpb = ctx->wpb;
     const int64_t spl = ctx->spl > 0 ? ctx->spl : n_steps;
@@ -2130,6 +2162,7 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
         cap = std::max(cap, ctxs[i]->hsys.cand_cap);
     }
     ws = WalkSet{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, (int)sys.size(), off.back()};
+    for (const SysDev& sd : sys) ws.gstride = std::max(ws.gstride, 2LL * sd.nca * sd.nav);
     if (sys.empty()) return 0;
     const int k = (int)sys.size();
     CK(cudaMemcpy(ctx->d_bsys, sys.data(), sizeof(SysDev) * k, cudaMemcpyHostToDevice));
@@ -2150,11 +2183,13 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int64_t n_
     if (graph && nfull > 0) {
         if (int r = walk_sort_prepare(ctx, ws.nslots)) return r;
         if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
+        if (int r = walk_gscr_prepare(ctx, ws.nslots * ws.gstride)) return r;
         mrq_ctx::GraphKey key;
         key.sys = ws.systems;
         key.wptr = ws.walkers;
         key.off = ws.offsets;
         key.keys = ctx->d_sort_keys;
+        key.gscr = ctx->d_gscr;
         key.nslots = ws.nslots;
         key.k = ws.nsys;
         key.wpb = wpb;

@@ -281,13 +281,62 @@ __device__ __forceinline__ double cand_sum(const SysDev& S, const unsigned long 
     return p0;
 }
 
-// <m|H|k> for a single candidate x -> y (x: lane's virtual electron or R', y: lane's hole or A')
+// The walker's single-excitation operator, for every hole y (core or active) and electron x (active
+// or virtual) of one spin s:  G^s_yx(n) = hc_yx + sum_{j in act occ(n)} (yx|jj) - sum_{j in act occ_s(n)} (yj|jx)
+// (n a CAS determinant: full core, empty virtuals).  Slater-Condon gives, for a neighbour
+// m = n - R + A and its single x -> y,  <k|H|m> = sign (G^s_yx(n) + sum_{j in A} f(j) - sum_{j in R} f(j)),
+// f(j) = (yx|jj) - d_{s_j s} (yj|jx): the same sum as single_elem over occ(m), with <= 4 corrections in
+// place of one term per occupied orbital.  g: 2 x nca x nav doubles, [s][y][x - nc]; the
+// active-active block is not needed (no single of a FOIS neighbour stays in the active space).
+template <class C>
+__device__ void walker_single_ops(const SysDev& S, unsigned long long AOn, double* __restrict__ g, int lane, C& ctr) {
+    const int nc = S.nc, na = S.na, n = S.n, nca = S.nca, nav = S.nav, blk = nca * nav;
+    for (int t = lane; t < 2 * blk; t += 32) {
+        const int sg = t >= blk, rem = t - sg * blk;
+        const int y = rem / nav, xo = rem - y * nav, x = nc + xo;
+        if (y >= nc && xo < na) continue;
+        ctr.g();
+        double v = __ldg(S.hc + y * n + x);
+        unsigned long long bits = AOn;
+        while (bits) {
+            const int b = __ffsll(bits) - 1;
+            bits &= bits - 1;
+            const int j = nc + (b & 31);
+            v += eri_g(S, y, x, j, j);
+            ctr.g();
+            if ((b >= 32) == (sg == 1)) {
+                v -= eri_g(S, y, j, j, x);
+                ctr.g();
+            }
+        }
+        g[t] = v;
+    }
+}
+
+// f(j) of one orbital j (spin orbital) for the single x -> y of spin sx (spatial px, py)
+__device__ __forceinline__ double single_corr(const SysDev& S, int sx, int px, int py, int j) {
+    const int sj = j >= S.n, pj = j - sj * S.n;
+    double v = eri_g(S, py, px, pj, pj);
+    if (sj == sx) v -= eri_g(S, py, pj, pj, px);
+    return v;
+}
+
+// <m|H|k> for a single candidate x -> y (x: lane's virtual electron or R', y: lane's hole or A');
+// with the walker's operator g (CAS walkers), from g and the corrections of m's removed (rm) and
+// added (ad) orbitals relative to n (r of each); else by the full Slater-Condon sum
 template <int W, class C>
-__device__ __forceinline__ double sgl_elem_code(const SysDev& S, const unsigned long long (&m)[2][W], unsigned code,
-                                                int nyv, int yv0, int nxc, int xc0, C& ctr) {
+__device__ __forceinline__ double sgl_elem_code(const SysDev& S, const double* g, const unsigned long long (&m)[2][W],
+                                                unsigned code, int nyv, int yv0, int nxc, int xc0, int r, int rm0,
+                                                int rm1, int ad0, int ad1, C& ctr) {
     const int x = nyv ? yv0 : act_so(S, (int)(code & 127u));
     const int y = nxc ? xc0 : act_so(S, (int)((code >> 14) & 127u));
-    return single_elem<W>(S, m, x, y, ctr);
+    if (g == nullptr) return single_elem<W>(S, m, x, y, ctr);
+    const int sx = x >= S.n, px = x - sx * S.n, py = y - sx * S.n;
+    double v = g[(sx * S.nca + py) * S.nav + (px - S.nc)];
+    v += single_corr(S, sx, px, py, ad0) - single_corr(S, sx, px, py, rm0);
+    if (r == 2) v += single_corr(S, sx, px, py, ad1) - single_corr(S, sx, px, py, rm1);
+    ctr.g(1 + 4 * r);
+    return sgn_single<W>(m[sx], px, py) * v;
 }
 
 // the cnt (1 or 2) items made of k1 "first" items (f0, f1) and then (s0, s1), sorted when cnt = 2
@@ -337,7 +386,7 @@ template <int W, int MODE, class C>
 __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, unsigned* ccode,
                                    const unsigned long long (&n)[2][W], double psin, unsigned step, unsigned wid,
                                    int lane, unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc,
-                                   mrq_neighbour* nbout, long long max_nb, C& ctr) {
+                                   mrq_neighbour* nbout, long long max_nb, C& ctr, double* gops) {
     build_lists<W>(S, n, sh, 0, 0, lane);          // occupied lists for the diagonal sums
     const int nc = S.nc, nv = S.nv, voff = S.nc + S.na;
     const double c0 = __ldg(S.c);
@@ -355,6 +404,10 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
     lane_acc_init<W>(acc, n);
     int nbase = 0;     // running neighbour index (debug records)
     PHASE_T0();
+    if (gops != nullptr) {
+        walker_single_ops(S, AOn, gops, lane, ctr);
+        __syncwarp();
+    }
 
     // (a) neighbours inside the CAS: active singles and doubles of n
     for (int r = 1; r <= 2; r++) {
@@ -508,7 +561,10 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                                            xa1, kb, ya0, ya1, r, xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1, m);
                                         double part = 0.0;
                                         for (int e = lane; e < n1; e += 32)
-                                            part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
+                                            part = fma(cphi[e],
+                                                       sgl_elem_code<W>(S, gops, m, ccode[e], v, yv0, c, xc0, r, rm0,
+                                                                        rm1, ad0, ad1, ctr),
+                                                       part);
                                         unsigned offd, offx;
                                         int par;
                                         lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
@@ -529,8 +585,13 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                     double om = hnm * phin;        // the k = n term
                                     if (wide) {
                                         double part = 0.0;
+                                        PHASE_ADD(3);
                                         for (int e = 0; e < n1; e++)
-                                            part = fma(cphi[e], sgl_elem_code<W>(S, m, ccode[e], v, yv0, c, xc0, ctr), part);
+                                            part = fma(cphi[e],
+                                                       sgl_elem_code<W>(S, gops, m, ccode[e], v, yv0, c, xc0, r, rm0,
+                                                                        rm1, ad0, ad1, ctr),
+                                                       part);
+                                        PHASE_ADD(7);
                                         unsigned offd, offx;
                                         int par;
                                         lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
