@@ -30,8 +30,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "cas10_56o"
 # DRAM bytes (read + write) per walker-step of k_walk on the 56-orbital workload, from one ncu
-# capture of a steady-state 4,096-walker launch (23.05 MB); null for other workloads
-TRAFFIC_PER_WALKER_STEP = {"cas10_56o": 23.053056e6 / 4096}
+# capture of a steady-state 4,096-walker launch (46.95 MB); null for other workloads
+TRAFFIC_PER_WALKER_STEP = {"cas10_56o": 46.953472e6 / 4096}
 METRIC = "walker-steps/s"
 # FP64 FMA pipe of GB300: 2 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12

@@ -67,7 +67,7 @@ int64_t footprint_of(const Request& r) {
     b += 8 * (2 * n * n + neri + npair * n * n + 2 * nca * nca * nav * nav + n + r.n_act * r.n_act);
     b += 16 * cap + 8 * nlab;
     b += 32 * G * nlab + 16 * G;        // N, U and the SC-MRCI gradient sums A, B per group
-    b += 64 * r.params.n_walkers + 16 * 8192;
+    b += (64 + 16 * nca * nav) * r.params.n_walkers + 16 * 8192;   // walkers and their single-excitation operators
     return b;
 }
 
