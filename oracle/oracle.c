@@ -818,11 +818,31 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out, double *Hll) {
         Nl[l] += buf[i].v * buf[i].v;
         pp += S->c[l] * S->c[l] * buf[i].v * buf[i].v;
     }
-    /* 2. <v_l|H_D|v_l> and <psi_s|H|psi_s> over pairs (m, m') H-connected */
+    /* 2. <v_l|H_D|v_l> and <psi_s|H|psi_s> over pairs (m, m') H-connected; the determinants are
+     * visited label by label, so that one thread owns a row of Hll (no shared writes) */
+    int64_t ntot = u + S->nref;
+    int64_t *lstart = calloc((size_t)(S->nlab + 1), sizeof(int64_t));
+    int64_t *lord = malloc(sizeof(int64_t) * (size_t)(ntot ? ntot : 1));
+    for (int64_t x = 0; x < ntot; x++) {
+        int64_t l = x < S->nref ? 0 : det_label(S, &buf[x - S->nref].d, NULL, NULL);
+        lstart[l + 1]++;
+    }
+    for (int64_t l = 0; l < S->nlab; l++) lstart[l + 1] += lstart[l];
+    {
+        int64_t *fill = malloc(sizeof(int64_t) * (size_t)(S->nlab + 1));
+        memcpy(fill, lstart, sizeof(int64_t) * (size_t)(S->nlab + 1));
+        for (int64_t x = 0; x < ntot; x++) {
+            int64_t l = x < S->nref ? 0 : det_label(S, &buf[x - S->nref].d, NULL, NULL);
+            lord[fill[l]++] = x;
+        }
+        free(fill);
+    }
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 1)
 #endif
-    for (int64_t i = -S->nref; i < u; i++) {
+    for (int64_t lgrp = 0; lgrp < S->nlab; lgrp++)
+    for (int64_t q = lstart[lgrp]; q < lstart[lgrp + 1]; q++) {
+        const int64_t i = lord[q] - S->nref;
         det_t d;
         double vi, ci;
         int64_t li;
@@ -831,12 +851,7 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out, double *Hll) {
         double dl = 0.0, ph = 0.0;
         if (li > 0) dl += hd_diag(S, &d) * vi * vi;
         ph += ci * vi * h_diag(S, &d) * ci * vi;
-        if (Hll) {
-#ifdef _OPENMP
-#pragma omp atomic
-#endif
-            Hll[li * S->nlab + li] += vi * h_diag(S, &d) * vi;
-        }
+        if (Hll) Hll[li * S->nlab + li] += vi * h_diag(S, &d) * vi;
         int occl[2 * MAXN], empl[2 * MAXN], no = 0, ne = 0;
         for (int so = 0; so < 2 * n; so++) { if (occ(&d, so, n)) occl[no++] = so; else empl[ne++] = so; }
         for (int kind = 1; kind <= 2; kind++)
@@ -854,12 +869,7 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out, double *Hll) {
                             else { int64_t j = find_dv(buf, u, &m); vm = j >= 0 ? buf[j].v : 0.0; }
                             if (vm == 0.0) continue;
                             ph += ci * vi * h_elem(S, &d, &m) * S->c[lm] * vm;
-                            if (Hll) {
-#ifdef _OPENMP
-#pragma omp atomic
-#endif
-                                Hll[li * S->nlab + lm] += vi * h_elem(S, &d, &m) * vm;
-                            }
+                            if (Hll) Hll[li * S->nlab + lm] += vi * h_elem(S, &d, &m) * vm;
                             if (li > 0 && lm == li) dl += vi * hd_elem(S, &d, &m) * vm;
                         }
         dla[i + S->nref] = dl;
@@ -870,6 +880,6 @@ int oracle_brute(void *h, double *Nl, double *Dl, double *out, double *Hll) {
         if (i >= 0) Dl[det_label(S, &buf[i].d, NULL, NULL)] += dla[i + S->nref];
     }
     out[0] = pp; out[1] = php; out[2] = (double)u;
-    free(buf); free(dla); free(pha);
+    free(buf); free(dla); free(pha); free(lstart); free(lord);
     return 0;
 }
