@@ -495,33 +495,17 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                 const int ne = rr - v, nf = rr - c;
                                 if (ne < 0 || nf < 0) continue;
                                 const int nA = nsub(cE, nf), tot = nsub(cO, ne) * nA;
-                                // candidates t in [0, tot): lanes first collect spin-balanced ones (fill),
-                                // then probe the reference together, every lane busy (consume)
-                                int tnext = 0;
-                                bool pend = false;
-                                unsigned long long Rb = 0, Ab = 0;
-                                while (true) {
-                                    while (tnext < tot) {
-                                        const unsigned idle = __ballot_sync(0xffffffffu, !pend);
-                                        if (idle == 0u) break;
-                                        if (!pend) {
-                                            const int t = tnext + __popc(idle & lt);
-                                            if (t < tot) {
-                                                const int iR = t / nA;
-                                                const unsigned long long r_ = subset_bits(AOm, cO, ne, iR);
-                                                const unsigned long long a_ = subset_bits(AEm, cE, nf, t - iR * nA);
-                                                if (sv + __popcll(r_ & 0xFFFFFFFFull) == sc + __popcll(a_ & 0xFFFFFFFFull)) {
-                                                    pend = true;
-                                                    Rb = r_;
-                                                    Ab = a_;
-                                                }
-                                            }
-                                        }
-                                        tnext += __popc(idle);
-                                    }
-                                    if (__ballot_sync(0xffffffffu, pend) == 0u) break;
-                                    bool valid = pend;
+                                for (int base = 0; base < tot; base += 32) {
+                                    const int t = base + lane;
+                                    bool valid = t < tot;
+                                    unsigned long long Rb = 0, Ab = 0;
                                     double phi = 0.0;
+                                    if (valid) {
+                                        const int iR = t / nA;
+                                        Rb = subset_bits(AOm, cO, ne, iR);
+                                        Ab = subset_bits(AEm, cE, nf, t - iR * nA);
+                                        valid = sv + __popcll(Rb & 0xFFFFFFFFull) == sc + __popcll(Ab & 0xFFFFFFFFull);
+                                    }
                                     if (valid) {
                                         const unsigned long long kact = (AOm & ~Rb) | Ab;
                                         const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
@@ -550,7 +534,6 @@ __device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, un
                                         }
                                     }
                                     count += __popc(vm);
-                                    pend = false;
                                 }
                             }
                             if (count > S.cand_cap) {
