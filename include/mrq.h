@@ -361,11 +361,14 @@ int mrq_mrci_gradient(mrq_ctx* ctx, double* grad, double* energy);
  */
 int mrq_amsgrad_step(mrq_ctx* ctx, double lr, double beta1, double beta2, double eps);
 
-/* Current coefficients c_l (n_labels doubles, host or device memory). */
+/* Current sampling coefficients c_l of Eq. 17 (after any AMSGrad steps): n_labels doubles into c
+ * (host or device memory, owned by the caller).  Errors: MRQ_INVALID_ARG (null), MRQ_NOT_LOADED. */
 int mrq_read_coeffs(mrq_ctx* ctx, double* c);
 
-/* Raw gradient sums of the last walk per walker group, n_groups x n_labels doubles each (host
- * memory; either may be NULL): accA[g][l] = sum w E_L / c_l, accB[g][l] = sum w / c_l. */
+/* Raw gradient sums of the last walk per walker group (Eq. 8-9 with residence weights w = 1/S),
+ * n_groups x n_labels doubles each, row-major by group (host memory owned by the caller; either
+ * may be NULL): accA[g][l] = sum w E_L / c_l, accB[g][l] = sum w / c_l.  n_groups is the last
+ * mrq_walkers_init's.  Errors: MRQ_NOT_LOADED (no walk yet). */
 int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB);
 
 /* Walker determinants (n_walkers x 2W words) and psi_s values; either may be NULL. */
