@@ -33,11 +33,11 @@ N_TYPES = 9          # type t = 3h + p of a determinant with h core holes and p 
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile oracle.c into oracle/_build/liboracle.so (gcc -O3 -std=c11: IEEE arithmetic, no FMA contraction; OpenMP)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -73,8 +73,19 @@ def _load():
             lib.oracle_philox.argtypes = [P, P, P]
             lib.oracle_walk_one.restype = C.c_int
             lib.oracle_walk_one.argtypes = [P, C.c_uint32, C.c_int64, C.c_uint64, P]
+            lib.oracle_set_threads.argtypes = [C.c_int]
+            lib.oracle_set_threads.restype = None
+            lib.oracle_neighbour_ids.restype = C.c_int64
+            lib.oracle_neighbour_ids.argtypes = [P, P, C.c_int64, P]
+            lib.oracle_neighbours.restype = C.c_int
+            lib.oracle_neighbours.argtypes = [P, P, C.c_int64, P, P, P]
             _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0):
+    """Threads of the oracle's parallel loops from now on (0: all cores)."""
+    _load().oracle_set_threads(int(n))
 
 
 def philox4x32_10(ctr, key):
@@ -172,6 +183,27 @@ class Oracle:
             r.update(dets=nd[:k], H=nv[:k, 0], HD=nv[:k, 1], O=nv[:k, 2], psi_m=nv[:k, 3], Gamma=nv[:k, 4],
                      exc=ne[:k])
         return r
+
+    def neighbour_ids(self, d):
+        """Excitation ids (r1 | r2<<8 | a1<<16 | a2<<24) of every neighbour of d, in the order of
+        local(); no overlaps are evaluated."""
+        dd = self._det(d)
+        n = self._lib.oracle_neighbour_ids(self._h, _ptr(dd), 0, None)
+        ids = np.zeros(max(n, 1), np.uint32)
+        self._lib.oracle_neighbour_ids(self._h, _ptr(dd), n, _ptr(ids))
+        return ids[:n]
+
+    def neighbours(self, d, ids):
+        """Per-neighbour quantities of local() for the given excitation ids of d:
+        dict(dets, H, HD, O, psi_m, Gamma), evaluated in parallel."""
+        dd = self._det(d)
+        ii = np.ascontiguousarray(ids, np.uint32)
+        dets = np.zeros((len(ii), 2 * self.W), np.uint64)
+        vals = np.zeros((len(ii), 5))
+        rc = self._lib.oracle_neighbours(self._h, _ptr(dd), len(ii), _ptr(ii), _ptr(dets), _ptr(vals))
+        if rc:
+            raise ValueError("an id is not a neighbour of the determinant")
+        return dict(dets=dets, H=vals[:, 0], HD=vals[:, 1], O=vals[:, 2], psi_m=vals[:, 3], Gamma=vals[:, 4])
 
     def move(self, d, seed: int, step: int, walker: int):
         nxt = np.zeros(2 * self.W, np.uint64)

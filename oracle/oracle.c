@@ -343,6 +343,16 @@ static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 
 void oracle_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox4x32_10(ctr, key, out); }
 
+/* threads of the parallel regions that follow (0 or less: the OpenMP default) */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    else omp_set_num_threads(omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* canonical excitation id: removed so r1<=r2, added a1<=a2 (singles repeat the orbital) */
 static uint32_t exc_id(int r1, int r2, int a1, int a2) {
     return (uint32_t)r1 | ((uint32_t)r2 << 8) | ((uint32_t)a1 << 16) | ((uint32_t)a2 << 24);
@@ -660,6 +670,83 @@ int64_t oracle_local(void *h, const uint64_t *x, double *out, int64_t max_nb, ui
     out[0] = L.S; out[1] = L.EL; out[2] = L.num; out[3] = L.Hnn; out[4] = L.HDnn; out[5] = L.psi_n;
     out[6] = (double)L.label; out[7] = (double)L.type; out[8] = (double)L.nnb; out[9] = (double)L.terms;
     return L.nnb;
+}
+
+/* The neighbour excitations of x (every spin-conserving single and double whose image m has
+ * |H| <= 2 and |P| <= 2, as in local_eval), ids exc_id(r1, r2, a1, a2) in local_eval's order; at
+ * most max are written.  Returns the count.  No overlaps are evaluated, so this is fast enough to
+ * list the millions of neighbours of a large determinant. */
+int64_t oracle_neighbour_ids(void *h, const uint64_t *x, int64_t max, uint32_t *ids) {
+    osys *S = (osys *)h;
+    const det_t d = det_from_words(S, x);
+    const int n = S->n;
+    int occl[2 * MAXN], empl[2 * MAXN], no = 0, ne = 0;
+    for (int so = 0; so < 2 * n; so++) { if (occ(&d, so, n)) occl[no++] = so; else empl[ne++] = so; }
+    int64_t cnt = 0;
+    for (int kind = 1; kind <= 2; kind++)
+        for (int x1 = 0; x1 < no; x1++)
+            for (int x2 = (kind == 1 ? x1 : x1 + 1); x2 < (kind == 1 ? x1 + 1 : no); x2++)
+                for (int y1 = 0; y1 < ne; y1++)
+                    for (int y2 = (kind == 1 ? y1 : y1 + 1); y2 < (kind == 1 ? y1 + 1 : ne); y2++) {
+                        int r1 = occl[x1], r2 = occl[x2], a1 = empl[y1], a2 = empl[y2];
+                        int sr = (r1 / n == 0) + (kind == 2 ? (r2 / n == 0) : 0);
+                        int sa = (a1 / n == 0) + (kind == 2 ? (a2 / n == 0) : 0);
+                        if (sr != sa) continue;
+                        det_t m = d;
+                        clrb(&m, r1, n); setb(&m, a1, n);
+                        if (kind == 2) { clrb(&m, r2, n); setb(&m, a2, n); }
+                        if (det_label(S, &m, NULL, NULL) < 0) continue;
+                        if (cnt < max) ids[cnt] = exc_id(r1, r2, a1, a2);
+                        cnt++;
+                    }
+    return cnt;
+}
+
+/* The per-neighbour quantities of local_eval for a given list of neighbours of x (ids as above):
+ * dets[k*2W..] = m, vals[k*5..] = H_nm, (H_D)_nm, O(m) | phi0(m), psi_s(m), Gamma_nm.  The
+ * neighbours are independent, so they are evaluated in parallel.  Returns 0, or -1 when an id is
+ * not a neighbour of x (a removed orbital empty, an added one occupied, spin not conserved, or an
+ * image outside CAS + FOIS). */
+int oracle_neighbours(void *h, const uint64_t *x, int64_t nid, const uint32_t *ids, uint64_t *dets,
+                      double *vals) {
+    osys *S = (osys *)h;
+    const det_t d = det_from_words(S, x);
+    const int n = S->n;
+    int hx, px;
+    const int64_t lx = det_label(S, &d, &hx, &px);
+    double on;
+    const double psi_n = psi_s(S, &d, &on);
+    int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+#endif
+    for (int64_t k = 0; k < nid; k++) {
+        const int r1 = ids[k] & 255u, r2 = (ids[k] >> 8) & 255u, a1 = (ids[k] >> 16) & 255u, a2 = (ids[k] >> 24) & 255u;
+        const int single = (r1 == r2);
+        if (r1 >= 2 * n || r2 >= 2 * n || a1 >= 2 * n || a2 >= 2 * n || (single != (a1 == a2)) ||
+            !occ(&d, r1, n) || !occ(&d, r2, n) || occ(&d, a1, n) || occ(&d, a2, n) ||
+            (r1 / n == 0) + (single ? 0 : (r2 / n == 0)) != (a1 / n == 0) + (single ? 0 : (a2 / n == 0))) {
+            bad = 1;
+            continue;
+        }
+        det_t m = d;
+        clrb(&m, r1, n); setb(&m, a1, n);
+        if (!single) { clrb(&m, r2, n); setb(&m, a2, n); }
+        const int64_t lm = det_label(S, &m, NULL, NULL);
+        if (lm < 0) { bad = 1; continue; }
+        double o;
+        const double ps = psi_s(S, &m, &o);
+        const double hnm = h_elem(S, &d, &m);
+        const double hd = (lx > 0 && lm == lx) ? hd_elem(S, &d, &m) : 0.0;
+        const double ratio = (psi_n != 0.0) ? ps / psi_n : 0.0;
+        det_to_words(S, &m, dets + k * 2 * S->W);
+        vals[k * 5 + 0] = hnm;
+        vals[k * 5 + 1] = hd;
+        vals[k * 5 + 2] = o;
+        vals[k * 5 + 3] = ps;
+        vals[k * 5 + 4] = fabs(hnm * ratio);
+    }
+    return bad ? -1 : 0;
 }
 
 /* One exponential-race move from x: writes the chosen determinant and returns its exc id. */

@@ -134,6 +134,25 @@ def test_neighbour_sets_brute_force(full):
         assert r["label"] == label_of(det, s)
 
 
+def test_neighbour_list_entries_reproduce_local(full):
+    """The list-only enumeration and the per-neighbour evaluation of a given list (used for the
+    large-system parity checks) give exactly what local() gives: same ids in the same order, the
+    same values bit for bit (the same arithmetic)."""
+    s, o, eri4, H, space = full
+    n = s.n_orb
+    dets = [d for d in space if label_of(d, s) >= 0][:12]
+    for det in dets:
+        x = Q.to_words(det, n)
+        r = o.local(x, max_nb=4096)
+        ids = o.neighbour_ids(x)
+        assert np.array_equal(ids, r["exc"])
+        got = o.neighbours(x, ids[::-1])
+        for k in ("dets", "H", "HD", "O", "psi_m", "Gamma"):
+            assert np.array_equal(got[k], r[k][::-1]), k
+    with pytest.raises(ValueError):
+        o.neighbours(Q.to_words(dets[0], n), np.array([0], np.uint32) | np.uint32(1 << 16))
+
+
 def test_reach_back_overlap_is_H_phi0(full):
     s, o, eri4, H, space = full
     n = s.n_orb
