@@ -29,14 +29,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "cas10_56o"
-# DRAM bytes (read + write) per walker-step of k_walk on the 56-orbital workload, from one ncu
-# capture of a steady-state 4,096-walker launch (46.95 MB); null for other workloads
-TRAFFIC_PER_WALKER_STEP = {"cas10_56o": 46.953472e6 / 4096}
+# DRAM bytes (read + write) per walker-step of the walk kernel, from an ncu capture of one
+# steady-state launch of the current kernel (None until one is taken)
+TRAFFIC_PER_WALKER_STEP = {}
 METRIC = "walker-steps/s"
 # FP64 FMA pipe of GB300: 2 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# random 8-byte loads from an L2-resident table, measured on this machine's GB300 (loads/s)
-L2_GATHER_PEAK = 3.14e11
 
 
 def parse():
@@ -49,17 +47,21 @@ def parse():
     ap.add_argument("--system", default=WORKLOAD, help="named synthetic workload of the plain path")
     ap.add_argument("--inner", type=int, default=1, help="walker steps per walk launch")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-walkers", type=int, default=8, help="walkers moved per timed step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
     ap.add_argument("--n-systems", type=int, default=64)
-    ap.add_argument("--n-requests", type=int, default=40)
+    ap.add_argument("--n-requests", type=int, default=24)
     ap.add_argument("--rate", type=float, default=20.0, help="request arrivals per second (served mode)")
-    ap.add_argument("--target-sigma", type=float, default=1e-3)
-    ap.add_argument("--req-walkers", type=int, default=512)
-    ap.add_argument("--req-max-steps", type=int, default=400)
+    ap.add_argument("--target-sigma", type=float, default=1e-4)
+    ap.add_argument("--req-walkers", type=int, default=2048)
+    ap.add_argument("--req-max-steps", type=int, default=4000)
     ap.add_argument("--max-active", type=int, default=16)
     ap.add_argument("--budget-gb", type=float, default=100.0)
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched sub-object out of the line")
+    ap.add_argument("--no-served", action="store_true", help="leave the served sub-object out of the line")
+    ap.add_argument("--batch-walkers", type=int, default=32768, help="walkers of the batched sub-object")
     return ap.parse_args()
 
 
@@ -149,26 +151,44 @@ def dist_env():
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(system, seconds: float, threads: int, orc=None):
-    """Walker-steps/s of the plain C oracle's walk on a bounded sample of the same workload."""
+def type_mix(orc, dets):
+    """Class mix (walkers per type 3h + p) of a set of determinants, by the oracle's labels."""
+    mix = [0] * 9
+    for d in dets:
+        _, h, p = orc.label(d)
+        mix[3 * h + p] += 1
+    return mix
+
+
+def cpu_oracle_steps(orc, dets, seconds: float, threads: int, seed: int = 3, step0: int = 0):
+    """Walker-steps/s of the plain C oracle on walker determinants `dets`: each one is one walker
+    step (local quantities of Eq. 5 and Eq. 16 with every reach-back overlap, then the move), the
+    oracle's own code as it stands, on `threads` cores.  Stops after `seconds` (at least one step).
+    Returns (rate, steps done, the moved determinants)."""
     import oracle as O
-    if orc is None:
-        orc = O.Oracle.from_system(system)
-    nw = max(threads, 1)
+    O.set_threads(threads)
+    moved = []
     t0 = time.perf_counter()
-    acc = orc.sample(nw, 1, 0, seed=3, n_groups=1, threads=threads)
-    t1 = time.perf_counter()
-    steps = 1
-    if (t1 - t0) < seconds / 3:
-        steps = max(1, int(seconds / max(t1 - t0, 1e-3)) - 1)
-        t0 = time.perf_counter()
-        acc = orc.sample(nw, steps, 0, seed=3, n_groups=1, threads=threads)
-        t1 = time.perf_counter()
-    ws = nw * steps
-    return ws / (t1 - t0), dict(walkers=nw, steps=steps, seconds=t1 - t0, type_steps=acc["type_steps"].tolist())
+    for w, d in enumerate(dets):
+        nxt, _, _ = orc.move(d, seed=seed, step=step0, walker=w)
+        moved.append(nxt)
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    O.set_threads(0)
+    return len(moved) / dt, len(moved), np.array(moved)
+
+
+def oracle_steady_dets(orc, n_walkers: int, warm_steps: int, seed: int):
+    """Walker determinants after `warm_steps` steps of the oracle's own walk from the start (the
+    steady-state class mix, for a CPU arm that has no GPU walkers to copy)."""
+    return np.array([orc.walk_one(w, warm_steps, seed)[-1] for w in range(n_walkers)])
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the benchmark's workload.  Each timed step
+    moves a bounded sample of walkers once (from the steady state of a short untimed warm-up walk),
+    on all of this host's cores."""
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -177,21 +197,25 @@ def run_reference(args):
     system = S.workload(args.system)
     threads = os.cpu_count() or 1
     orc = O.Oracle.from_system(system)
-    per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
+    nw = args.ref_walkers
+    dets = oracle_steady_dets(orc, nw, 3, seed=11)
+    mix = type_mix(orc, dets)
     rates = []
-    meta = None
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
     for k in range(args.warmup + args.steps):
-        r, meta = cpu_oracle_rate(system, per_step, threads, orc)
+        r, done, moved = cpu_oracle_steps(orc, dets, per_step, threads, seed=11, step0=3 + k)
+        dets = np.concatenate([moved, dets[done:]]) if done < len(dets) else moved
         if k >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * meta["walkers"] * meta["steps"] / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * nw / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.system, "walkers_per_step": meta["walkers"], "steps_per_walker": meta["steps"]},
+        "config": {"workload": args.system, "walkers_per_step": nw, "class_mix_at_start": mix},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
-                         "sample": f"{meta['walkers']} walkers x {meta['steps']} steps per timed step"},
+                         "sample": f"{nw} walkers per timed step (at most {per_step:.0f} s each), one walker step "
+                                   f"each, from the state after a 3-step untimed oracle walk (class mix {mix})"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -268,21 +292,27 @@ def run_ours(args):
     flops_per_step = 2.0 * terms + 8.0 * nbrs
     launch_s = walk_s / max(walk_launches, 1)
     units_per_launch = nw * inner
-    fp64_peak = FP64_PEAK_TFLOPS
     achieved = flops_per_step * units_per_launch / launch_s / 1e12
     peaks, peak_kind = load_peaks()
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak,
+    probe = P.probe_peaks(local)
+    sectors_per_s = gathers * units_per_launch / launch_s
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": (TRAFFIC_PER_WALKER_STEP[args.system] * units_per_launch
                         if args.system in TRAFFIC_PER_WALKER_STEP else None),
-            "kernel": "k_walk",
-            "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (probe on this pool: 1.254 TFLOP/s)",
+            "kernel": "k_walk2",
+            "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from unit counts and the "
+                           "maximum SM clock)",
+            "peak_measured": probe["fp64_flops"] / 1e12,
+            "frac_of_measured": achieved / (probe["fp64_flops"] / 1e12),
             "flops_per_walker_step": flops_per_step, "terms_per_walker_step": terms,
-            "launch_seconds": launch_s, "launches_timed": int(walk_launches),
-            "gathers_per_walker_step": gathers,
-            "l2_gather_rate_per_s": gathers * units_per_launch / launch_s,
-            "l2_gather_peak_per_s": L2_GATHER_PEAK, "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-            "hbm_peak_source": peak_kind}
+            "neighbours_per_walker_step": nbrs, "launch_seconds": launch_s, "launches_timed": int(walk_launches),
+            # the gather view of the same launches: every integral / table gather and hash-slot read is
+            # one random 32-byte sector (the algorithmic sectors of the walk)
+            "sectors_per_walker_step": gathers, "sectors_per_s": sectors_per_s,
+            "l2_gather_peak_per_s": probe["l2_gathers_per_s"], "hbm_gather_peak_per_s": probe["hbm_gathers_per_s"],
+            "l2_frac": sectors_per_s / probe["l2_gathers_per_s"],
+            "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_kind}
     cand_per_step = float(np.mean([np.mean(l["n_candidates"]) for l in locs]))
     nb_per_step = nbrs
 
@@ -317,11 +347,28 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on the GPU walkers' own steady-state determinants (the same class mix), on all
+        # host cores and on one core
+        import oracle as O
+        orc = O.Oracle.from_system(system)
         threads = os.cpu_count() or 1
-        rate, meta = cpu_oracle_rate(system, args.cpu_seconds, threads)
+        sample = snap1[:64]
+        rate, done, _ = cpu_oracle_steps(orc, sample, args.cpu_seconds, threads)
+        rate1, done1, _ = cpu_oracle_steps(orc, sample, args.cpu_seconds / 2, 1)
+        mix = type_mix(orc, sample[:done])
         cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
-               "sample": f"{meta['walkers']} walkers x {meta['steps']} steps of the same workload "
-                         f"({meta['seconds']:.1f} s; class mix {meta['type_steps']})"}
+               "one_core": {"value": rate1, "steps": done1},
+               "sample": f"{done} walker steps of the oracle (local quantities with every reach-back overlap, "
+                         f"then the move) from the GPU walkers' determinants after the timed region "
+                         f"(class mix {mix}), at most {args.cpu_seconds:.0f} s; one core: {done1} steps"}
+
+    # the metric's other half: batched and served against plain, on their own workloads
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = measure_batched(args.n_systems, args.batch_walkers, R=1, steps=2, warmup=1)
+    if rank == 0 and world == 1 and not args.no_served:
+        served = measure_served(args.n_requests, args.rate, args.target_sigma, args.req_walkers, args.req_max_steps,
+                                args.max_active, args.budget_gb)
 
     if rank == 0:
         line = {
@@ -340,8 +387,11 @@ def run_ours(args):
             "clocks": clk.summary(),
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,        # per step: walk, finalize-labels, finalize-reduce
+            # per step: slot keys, slot sort, walk, accumulate; finalize labels, finalize reduce
+            "gpu_launches": 6 * args.steps,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -350,13 +400,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """Plain (one system per launch) against batched (all systems in one launch) on the batched
-    workload: 64 seeded systems, 30-120 orbitals, CAS(6..10) references, walkers proportional to
-    reference size (32,768 in total)."""
+def measure_batched(n_systems: int, total_walkers: int, R: int, steps: int, warmup: int, max_act: int = 14):
+    """Walker-steps/s of the batched workload (seeded systems of 30-120 orbitals, active spaces
+    6-max_act, references of 400 to 5e5 determinants, walkers proportional to the reference size)
+    run three ways with the same reporting interval of R walker steps (one finalize per system):
+    plain (one system per launch, one after the other), batched (every system in one launch per
+    determinant width) and batched with the autotuned launch configuration and CUDA-graph replay."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     import synthetic as S
-    specs, walkers = S.batch_specs(args.n_systems)
+    specs, walkers = S.batch_specs(n_systems, total_walkers=total_walkers, max_act=max_act)
     t0 = time.perf_counter()
     systems = S.make_systems(specs, processes=min(16, os.cpu_count() or 1))
     t_gen = time.perf_counter() - t0
@@ -366,8 +418,6 @@ def run_batched(args):
     ctxs = [P.Context.from_system(s) for s in systems]
     params = [c.params(nw, 0, burn_in=0, seed=500 + k, n_groups=8) for k, (c, nw) in enumerate(zip(ctxs, walkers))]
     total = sum(walkers)
-
-    R = max(1, args.inner)      # walker steps per reporting interval (one finalize per system)
 
     def plain_step():
         for c in ctxs:
@@ -384,70 +434,99 @@ def run_batched(args):
         for c, p in zip(ctxs, params):
             c.walkers_init(p)
             c.set_launch()
-        if name == "batched_tuned":     # autotune walkers/block and steps/launch, then graph replay
+        if name == "batched_tuned":     # autotune warps per walker and steps per launch, then graph replay
             tune = P.tune_batch(ctxs, trial_steps=min(R, 16))
             for c in ctxs:
-                c.set_launch(tune["warps_per_block"], min(tune["steps_per_launch"], R), True)
-        for _ in range(args.warmup):
+                c.set_launch(tune["warps_per_walker"], min(tune["steps_per_launch"], R), True)
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         torch.cuda.synchronize(dev)
-        out[name] = total * R * args.steps / (time.perf_counter() - t0)
+        out[name] = total * R * steps / (time.perf_counter() - t0)
     for c in ctxs:
         c.set_launch()
-    line = {"metric": METRIC, "mode": "batched", "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "plain": out["plain"], "batched": out["batched"],
-            "batched_tuned": out["batched_tuned"], "speedup": out["batched"] / out["plain"],
-            "speedup_tuned": out["batched_tuned"] / out["plain"], "tuned_launch": tune,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batch{args.n_systems}", "systems": args.n_systems, "walkers": total,
-                       "steps_per_report": R,
+        c.close()
+    return {"plain": out["plain"], "batched": out["batched"], "batched_tuned": out["batched_tuned"],
+            "speedup": out["batched"] / out["plain"], "speedup_tuned": out["batched_tuned"] / out["plain"],
+            "unit": METRIC, "tuned_launch": tune, "steps": steps, "warmup": warmup, "steps_per_report": R,
+            "config": {"workload": f"batch{n_systems}", "systems": n_systems, "walkers": total,
+                       "active_orbitals": sorted({s.n_act for s in systems}),
                        "orbitals": [s.n_orb for s in systems], "reference_dets": [len(s.coeffs) for s in systems],
                        "generation_seconds": t_gen}}
+
+
+def run_batched(args):
+    """The batched workload at full size (64 systems, 32,768 walkers) as its own JSON line."""
+    r = measure_batched(args.n_systems, 32768, max(1, args.inner), args.steps, args.warmup)
+    line = {"metric": METRIC, "mode": "batched", "n_gpus": 1, "dtype": "f64", "data": "synthetic", **r}
     print(json.dumps(line), flush=True)
+
+
+def served_pool(n_requests: int, seed: int = 77):
+    """The served request stream: small seeded systems (12-24 orbitals, CAS(4..6) references) and a
+    10-point geometry scan of one 22-orbital system (one orbital partition, L(lambda) = L0 + lambda dL),
+    in a seeded random order."""
+    import synthetic as S
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = dict(n_core=2, n_act=6, n_virt=14, n_alpha=5, n_beta=5, rank=66, seed=3301, chol_sigma=0.06)
+    pool = [S.workload("tiny_12o_cas4")]
+    pool += [S.make_system(2 + k % 2, 4 + 2 * (k % 2), 8 + 3 * k, 2 + k % 2 + (2 + k % 2), 2 + k % 2 + (2 + k % 2),
+                           rank=36 + 9 * k, seed=3400 + k, chol_sigma=0.06) for k in range(4)]
+    scan = S.scan_systems(base, n_points=10)
+    reqs = [pool[int(rng.integers(len(pool)))] for _ in range(max(0, n_requests - len(scan)))] + scan
+    return [reqs[k] for k in rng.permutation(len(reqs))], len(scan)
+
+
+def measure_served(n_requests: int, rate: float, target: float, req_walkers: int, max_steps: int,
+                   max_active: int, budget_gb: float, steps_per_round: int = 20, seed: int = 77):
+    """Time to a target sigma of E^(2) for a Poisson stream of requests, served (continuous batching,
+    up to max_active requests resident) and plain (the same stream, one request resident at a time,
+    first come first served).  Returns both with p50 / p99 time to target and throughput."""
+    import paper_1909_06935_gb300 as P
+    reqs, n_scan = served_pool(n_requests, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+
+    def one(active):
+        srv = P.Server(max_active=active, hbm_budget_bytes=int(budget_gb * (1 << 30)), steps_per_round=steps_per_round)
+        srv.start()
+        t0 = time.perf_counter()
+        tickets = []
+        for k, s in enumerate(reqs):
+            tickets.append(srv.submit(s, req_walkers, max_steps, target_sigma=target, burn_in=20, seed=900 + k,
+                                      n_groups=16))
+            time.sleep(gaps[k])
+        while not all(srv.poll(t)["state"] in ("done", "failed", "cancelled") for t in tickets):
+            time.sleep(0.02)
+        wall = time.perf_counter() - t0
+        srv.stop()
+        st = [srv.poll(t) for t in tickets]
+        steps = srv.info()["walker_steps"]
+        srv.close()
+        tt = np.array([x["total_seconds"] for x in st])
+        reached = int(sum(x["result"]["e2_sigma"] <= target for x in st))
+        return {"p50_s": float(np.percentile(tt, 50)), "p99_s": float(np.percentile(tt, 99)),
+                "reached_target": reached, "requests": len(st), "throughput_req_per_s": len(st) / wall,
+                "walker_steps_per_s": steps / wall, "failed": int(sum(x["state"] == "failed" for x in st))}
+
+    served = one(max_active)
+    plain = one(1)
+    return {"metric": "time-to-target", "unit": "s", "target_sigma": target, "arrival_rate": rate,
+            "served": served, "plain": plain,
+            "p50_speedup": plain["p50_s"] / served["p50_s"], "p99_speedup": plain["p99_s"] / served["p99_s"],
+            "config": {"workload": "served", "requests": len(reqs), "scan_points": n_scan,
+                       "orbitals": sorted({int(s.n_orb) for s in reqs}),
+                       "request_walkers": req_walkers, "max_steps": max_steps, "max_active": max_active,
+                       "steps_per_round": steps_per_round}}
 
 
 def run_served(args):
-    """Poisson stream of sampling requests through the request server (continuous batching):
-    p50 / p99 time to the target error of E^(2), and throughput."""
-    import synthetic as S
-    import paper_1909_06935_gb300 as P
-    rng = np.random.Generator(np.random.PCG64(77))
-    base = dict(n_core=2, n_act=6, n_virt=16, n_alpha=5, n_beta=5, rank=72, seed=3301, chol_sigma=0.06)
-    pool = [S.workload("tiny_12o_cas4")]
-    pool += [S.make_system(2 + k % 3, 4 + 2 * (k % 2), 8 + 4 * k, 2 + k % 3 + (2 + k % 2), 2 + k % 3 + (2 + k % 2),
-                           rank=40 + 8 * k, seed=3400 + k, chol_sigma=0.06) for k in range(6)]
-    scan = S.scan_systems(base, n_points=10)
-    reqs = [pool[int(rng.integers(len(pool)))] for _ in range(args.n_requests - len(scan))] + scan
-    order = rng.permutation(len(reqs))
-    srv = P.Server(max_active=args.max_active, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), steps_per_round=2)
-    srv.start()
-    t0 = time.perf_counter()
-    tickets = []
-    for k in order:
-        tickets.append(srv.submit(reqs[k], args.req_walkers, args.req_max_steps, target_sigma=args.target_sigma,
-                                  burn_in=10, seed=900 + int(k), n_groups=16))
-        time.sleep(rng.exponential(1.0 / args.rate))
-    while not all(srv.poll(t)["state"] in ("done", "failed", "cancelled") for t in tickets):
-        time.sleep(0.02)
-    wall = time.perf_counter() - t0
-    srv.stop()
-    st = [srv.poll(t) for t in tickets]
-    tt = np.array([x["total_seconds"] for x in st])
-    reached = np.array([x["result"]["e2_sigma"] <= args.target_sigma for x in st])
-    steps = sum(x["result"]["walker_steps"] for x in st)
-    line = {"metric": "time-to-target", "mode": "served", "unit": "s", "p50": float(np.percentile(tt, 50)),
-            "p99": float(np.percentile(tt, 99)), "requests": len(st), "reached_target": int(reached.sum()),
-            "throughput_req_per_s": len(st) / wall, "walker_steps_per_s": srv.info()["walker_steps"] / wall,
-            "accumulated_walker_steps": int(steps), "target_sigma": args.target_sigma, "arrival_rate": args.rate,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "served", "request_walkers": args.req_walkers, "max_steps": args.req_max_steps,
-                       "max_active": args.max_active, "scan_points": len(scan)}}
-    print(json.dumps(line), flush=True)
-    srv.close()
+    r = measure_served(args.n_requests, args.rate, args.target_sigma, args.req_walkers, args.req_max_steps,
+                       args.max_active, args.budget_gb)
+    print(json.dumps({"mode": "served", "n_gpus": 1, "dtype": "f64", "data": "synthetic", **r}), flush=True)
 
 
 def main():

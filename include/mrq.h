@@ -67,7 +67,8 @@ typedef struct {
     int32_t n_groups;       /* G walker groups for jackknife errors (walker w is in group w mod G) */
     int32_t method;         /* mrq_method: informative; both estimators are always accumulated */
     double screen_tau;      /* perturbers with N_l/N_0 below this are screened out (Sec. II C) */
-    int32_t walkers_per_block; /* 1, 2 or 4 walkers per thread block; 0 keeps the context's setting */
+    int32_t warps_per_walker;  /* 1, 2, 4 or 8 warps in each walker's thread block; 0 keeps the context's
+                                  setting (by default chosen from the system's size, see mrq_set_launch) */
     int32_t steps_per_check;   /* mrq_sample with target_sigma: steps between error checks (0: n_steps/16) */
     double target_sigma;    /* mrq_sample stops early once the jackknife sigma of E^(2) (method
                                SC_NEVPT2) or of E (SC_MRCI) is at or below this; 0 = off */
@@ -231,28 +232,31 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps);
 /*
  * Launch configuration of a context's walks (no counterpart in the paper: a GPU scheduling
  * choice that leaves every trajectory and accumulator the same, up to the order of the FP64
- * additions).  warps_per_block in {1, 2, 4} walkers per thread block (default 4);
+ * additions).  warps_per_walker in {1, 2, 4, 8}: the warps of the thread block that takes one walker's
+ * step (they split its neighbours into interleaved work units); 0, the default, chooses from the
+ * system's work units per CAS walker (8 for 512 or more, 4 for 128 or more, else 2; a batch takes
+ * the largest of its systems' choices);
  * steps_per_launch >= 1 splits an advance into launches of that many steps, each re-ordering the
  * walker slots first (0, the default: one launch per advance); use_graph != 0 makes
  * mrq_batch_advance, with ctxs[0] this context, capture one launch of steps_per_launch steps (the
  * reporting interval: slot sort + walk) into a CUDA graph once per batch layout and replay it.
  * Errors: MRQ_INVALID_ARG.
  */
-int mrq_set_launch(mrq_ctx* ctx, int warps_per_block, int steps_per_launch, int use_graph);
+int mrq_set_launch(mrq_ctx* ctx, int warps_per_walker, int steps_per_launch, int use_graph);
 
 #define MRQ_TUNE_MAX 16
 typedef struct {
-    int warps_per_block;      /* the fastest configuration, now set on every context of the batch */
+    int warps_per_walker;     /* the fastest configuration, now set on every context of the batch */
     int steps_per_launch;
     int n_tried;
-    int tried_warps_per_block[MRQ_TUNE_MAX];
+    int tried_warps_per_walker[MRQ_TUNE_MAX];
     int tried_steps_per_launch[MRQ_TUNE_MAX];
     double tried_ms[MRQ_TUNE_MAX];   /* device time of trial_steps steps, best of up to 3 */
 } mrq_tune_result;
 
 /*
  * Autotuner of the batched walk: times trial_steps (1..1024) steps of the batch for every
- * warps_per_block in {1, 2, 4} and steps_per_launch in {1, 4, 16} (those <= trial_steps), on a
+ * warps_per_walker in {2, 4, 8} and steps_per_launch in {1, 4, 16} (those <= trial_steps), on a
  * scratch copy of the walkers with accumulation off, so the contexts' walkers and accumulators
  * are left as they were; then sets the fastest pair on every context (mrq_set_launch, keeping
  * use_graph).  out may be NULL.  Errors: as mrq_batch_advance, MRQ_INVALID_ARG for trial_steps.
@@ -373,6 +377,64 @@ int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB);
 
 /* Walker determinants (n_walkers x 2W words) and psi_s values; either may be NULL. */
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi);
+
+/*
+ * The two clocks of the move race (Sec. II B: the rejection-free continuous-time walk, taken in
+ * the first-reaction form of Gillespie's algorithm; each neighbour m draws t = -ln(u)/Gamma_nm
+ * and the smallest t wins), for parity tests of the screen that decides which candidates need
+ * the exact clock.  For i < n: u = (k53[i] + 1) 2^-53 with k53[i] < 2^53 (the 53 random bits of
+ * the walk's Philox4x32-10 draw), exact[i] = -ln(u)/rate[i] in FP64, and screen[i] the FP32
+ * clock the walk compares first, formed as the walk forms it: within 1e-6 relative of exact[i]
+ * for 1e-30 < rate < 1e30 and clocks above 1e-37, and 0 (which never screens a candidate out)
+ * otherwise.  All arrays are n long, host or
+ * device memory owned by the caller.  Errors: MRQ_INVALID_ARG (null pointers, n <= 0, a k53
+ * with more than 53 bits), MRQ_CUDA_ERROR.
+ */
+int mrq_debug_race_clocks(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, float* screen,
+                          double* exact);
+
+/*
+ * Persisting-L2 window of this context's walk launches (no counterpart in the paper; a GB300
+ * cache setting).  With fraction > 0 every walk launch marks the physicists' integral tables (the
+ * entries every reach-back term reads) as persisting in L2, with a hit ratio that fits them into
+ * fraction x the device's maximum persisting carve-out, which this call's launches set as the
+ * CUDA context's persisting-L2 limit (a per-process limit that ends with the context; no device
+ * setting outlasts the process).  0 (the default) launches without a window.  Batched launches
+ * (several systems) never take one.  Errors: MRQ_INVALID_ARG (fraction outside [0, 1]).
+ */
+int mrq_set_l2_window(mrq_ctx* ctx, double fraction);
+
+/*
+ * Deadline of this context's host waits (failure detection; the paper has no counterpart).
+ * With seconds > 0, every call that waits for the device (mrq_finalize, mrq_finalize_noalloc,
+ * mrq_sample, the readers, and the wait for earlier work at the start of a load) gives up after
+ * that long and returns MRQ_DEVICE_TIMEOUT; nothing is written to its outputs, the device work
+ * keeps running, and the next call waits for it again.  Set-up calls apply the deadline only to
+ * the wait for earlier work, never to their own kernels.  0 (the default) waits without limit.
+ * Errors: MRQ_INVALID_ARG (negative).
+ */
+int mrq_set_deadline(mrq_ctx* ctx, double seconds);
+
+/*
+ * Lower the walk's device-side bounds, so that tests can make them run out (failure detection;
+ * the paper has no counterpart).  max_probe (1..64) bounds the hash slots a lookup reads (the
+ * table itself allows 64); cand_cap bounds the entries of one candidate list of the grouped
+ * CAS-walker path (at most what the loaded system needs).  A lookup or list that runs past its
+ * bound sets a device flag and the next finalize returns MRQ_HASH_OVERFLOW or MRQ_TOO_LARGE; the
+ * walk itself always ends (the overflowing lookup reads as absent, the list is cut).  0 restores
+ * the default of either.  A bound lowered before mrq_load_reference also bounds the table's
+ * insertions.  Errors: MRQ_INVALID_ARG.
+ */
+int mrq_debug_set_limits(mrq_ctx* ctx, int max_probe, int cand_cap);
+
+/*
+ * Measured ceilings of the device for the walk's roofline (the paper has no counterpart): the walk
+ * is FP64 arithmetic on randomly gathered table entries.  out3[0] = FP64 FMA rate (flop/s) of
+ * independent register FMA chains on every SM; out3[1] = random 8-byte reads per second from a
+ * 16 MiB table (resident in L2); out3[2] = the same from a 4 GiB table (HBM).  Allocates and frees
+ * 4 GiB on `device`, runs for about a tenth of a second.  Errors: MRQ_INVALID_ARG, MRQ_CUDA_ERROR.
+ */
+int mrq_probe_peaks(int device, double* out3);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,7 @@ __all__ = ["Context", "SampleParams", "Result", "Local", "Neighbour", "MRQError"
            "TYPE_NAMES", "n_labels", "batch_advance", "sample_batch"]
 
 NTYPES = 9
+NOALLOC_SCRATCH_DOUBLES = 1 << 19     # fixed scratch of mrq_finalize_noalloc (include/mrq.h)
 TYPE_NAMES = ["CAS", "S_r", "S_rs", "S_i", "S_ir", "S_irs", "S_ij", "S_ijr", "S_ijrs"]   # index 3h + p
 SC_NEVPT2, SC_MRCI = 0, 1
 
@@ -25,7 +26,7 @@ SC_NEVPT2, SC_MRCI = 0, 1
 class SampleParams(C.Structure):
     _fields_ = [("n_walkers", C.c_int64), ("n_steps", C.c_int64), ("burn_in", C.c_int64), ("seed", C.c_uint64),
                 ("n_groups", C.c_int32), ("method", C.c_int32), ("screen_tau", C.c_double),
-                ("walkers_per_block", C.c_int32), ("steps_per_check", C.c_int32), ("target_sigma", C.c_double)]
+                ("warps_per_walker", C.c_int32), ("steps_per_check", C.c_int32), ("target_sigma", C.c_double)]
 
 
 class Result(C.Structure):
@@ -72,14 +73,14 @@ TUNE_MAX = 16
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("warps_per_block", C.c_int32), ("steps_per_launch", C.c_int32), ("n_tried", C.c_int32),
-                ("tried_warps_per_block", C.c_int32 * TUNE_MAX), ("tried_steps_per_launch", C.c_int32 * TUNE_MAX),
+    _fields_ = [("warps_per_walker", C.c_int32), ("steps_per_launch", C.c_int32), ("n_tried", C.c_int32),
+                ("tried_warps_per_walker", C.c_int32 * TUNE_MAX), ("tried_steps_per_launch", C.c_int32 * TUNE_MAX),
                 ("tried_ms", C.c_double * TUNE_MAX)]
 
     def as_dict(self):
         n = self.n_tried
-        return dict(warps_per_block=self.warps_per_block, steps_per_launch=self.steps_per_launch,
-                    tried=[(self.tried_warps_per_block[i], self.tried_steps_per_launch[i], self.tried_ms[i])
+        return dict(warps_per_walker=self.warps_per_walker, steps_per_launch=self.steps_per_launch,
+                    tried=[(self.tried_warps_per_walker[i], self.tried_steps_per_launch[i], self.tried_ms[i])
                            for i in range(n)])
 
 
@@ -132,14 +133,31 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_read_coeffs.argtypes = [P, P]
     lib.mrq_read_gradient_sums.argtypes = [P, P, P]
     lib.mrq_sample_batch.argtypes = [P, C.c_int, P, P]
+    lib.mrq_debug_race_clocks.argtypes = [P, I64, P, P, P, P]
+    lib.mrq_set_deadline.argtypes = [P, C.c_double]
+    lib.mrq_probe_peaks.argtypes = [C.c_int, P]
+    lib.mrq_set_l2_window.argtypes = [P, C.c_double]
+    lib.mrq_debug_set_limits.argtypes = [P, C.c_int, C.c_int]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
                "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch", "mrq_mrci_gradient",
                "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_set_launch",
-               "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers"):
+               "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers", "mrq_debug_race_clocks",
+               "mrq_set_deadline", "mrq_debug_set_limits", "mrq_probe_peaks",
+               "mrq_set_l2_window"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
+
+
+def probe_peaks(device: int = 0) -> dict:
+    """Measured FP64 FMA rate and random 8-byte read rates (L2- and HBM-resident tables) of the device."""
+    lib = load_library()
+    out = np.zeros(3)
+    rc = lib.mrq_probe_peaks(device, out.ctypes.data_as(C.c_void_p))
+    if rc:
+        raise MRQError(rc, "mrq_probe_peaks failed")
+    return dict(fp64_flops=float(out[0]), l2_gathers_per_s=float(out[1]), hbm_gathers_per_s=float(out[2]))
 
 
 def n_labels(n_core: int, n_virt: int) -> int:
@@ -254,8 +272,8 @@ class Context:
         return loc, (nb.reshape(n, max_nb) if max_nb else None)
 
     def params(self, n_walkers, n_steps, burn_in=0, seed=1, n_groups=16, screen_tau=1e-10, method=SC_NEVPT2,
-               walkers_per_block=0, target_sigma=0.0, steps_per_check=0):
-        return SampleParams(n_walkers, n_steps, burn_in, seed, n_groups, method, screen_tau, walkers_per_block,
+               warps_per_walker=0, target_sigma=0.0, steps_per_check=0):
+        return SampleParams(n_walkers, n_steps, burn_in, seed, n_groups, method, screen_tau, warps_per_walker,
                             steps_per_check, target_sigma)
 
     def walkers_init(self, p: SampleParams):
@@ -290,10 +308,11 @@ class Context:
         self._check(self._lib.mrq_read_accumulators(self._h, _addr(N), _addr(U), _addr(Wg), _addr(E), _addr(ts)))
         return dict(N=N, U=U, W=Wg, E=E, type_steps=ts)
 
-    def set_launch(self, warps_per_block=4, steps_per_launch=0, use_graph=False):
-        """Walk launch configuration: walkers per block, steps per launch (0 = one launch per
-        advance), CUDA-graph replay of batched reporting intervals."""
-        self._check(self._lib.mrq_set_launch(self._h, warps_per_block, steps_per_launch, int(bool(use_graph))))
+    def set_launch(self, warps_per_walker=0, steps_per_launch=0, use_graph=False):
+        """Walk launch configuration: warps per walker block (0 = chosen from the system's size),
+        steps per launch (0 = one launch per advance), CUDA-graph replay of batched reporting
+        intervals."""
+        self._check(self._lib.mrq_set_launch(self._h, warps_per_walker, steps_per_launch, int(bool(use_graph))))
 
     def mrci_gradient(self):
         """SC-MRCI(s) gradient (Eq. 8-9) of the last walk and the energy estimate."""
@@ -330,6 +349,29 @@ class Context:
             self.amsgrad_step(lr, beta1, beta2, eps)
             hist.append(res)
         return hist
+
+    def set_l2_window(self, fraction: float):
+        """Mark the integral tables persisting in L2 for this context's walks (0 turns it off)."""
+        self._check(self._lib.mrq_set_l2_window(self._h, float(fraction)))
+
+    def set_deadline(self, seconds: float):
+        """Host waits of this context give up after `seconds` (0: no deadline) with MRQError(-6)."""
+        self._check(self._lib.mrq_set_deadline(self._h, float(seconds)))
+
+    def debug_set_limits(self, max_probe: int = 0, cand_cap: int = 0):
+        """Lower the hash-probe bound and the candidate-list capacity (0 restores the default)."""
+        self._check(self._lib.mrq_debug_set_limits(self._h, int(max_probe), int(cand_cap)))
+
+    def race_clocks(self, k53, rate):
+        """The move race's FP32 screening clock and exact FP64 clock for (k53, rate) pairs."""
+        k = np.ascontiguousarray(k53, np.uint64)
+        r = np.ascontiguousarray(rate, np.float64)
+        if k.shape != r.shape:
+            raise ValueError("k53 and rate must have the same shape")
+        scr = np.zeros(k.shape, np.float32)
+        ex = np.zeros(k.shape, np.float64)
+        self._check(self._lib.mrq_debug_race_clocks(self._h, k.size, _addr(k), _addr(r), _addr(scr), _addr(ex)))
+        return scr, ex
 
     def walkers(self, n_walkers: int):
         d = np.zeros((n_walkers, 2 * self.W), np.uint64)

@@ -14,7 +14,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/mrq.h"
@@ -29,6 +32,11 @@ struct Walker {
     unsigned wid;                 // walker id (Philox counter word)
     int sys;                      // index into the system table
     int group;                    // accumulator group
+    // the last step's contribution, written by the walk and added by k_accum
+    long long rl;                 // label of the determinant the step was taken at (-1: nothing to add)
+    double rw, rEL, rnum;         // residence weight 1/S, E_L, H_D numerator
+    int rtype;                    // 3h + p
+    int rpad;
 };
 
 static_assert(sizeof(SysDev) % sizeof(int) == 0, "SysDev is copied word by word");
@@ -283,202 +291,7 @@ __device__ void diagonals(const SysDev& S, const WarpSh& sh, const unsigned long
 
 enum { MODE_STEP = 0, MODE_DEBUG = 1 };
 
-struct LocalOut {
-    double S, EL, num, hnn, hdnn;
-    int nnb;
-};
-
-// per-lane partial results of one local evaluation
-template <int W>
-struct LaneAcc {
-    double sS, sH, sHD;
-    double bt;          // best (smallest) exponential clock
-    float btf;          // its FP32 image, for screening
-    unsigned bexc;
-    double bpsi;
-    unsigned long long bm[2][W];
-};
-
-template <int W>
-__device__ __forceinline__ void lane_acc_init(LaneAcc<W>& a, const unsigned long long (&n)[2][W]) {
-    a.sS = a.sH = a.sHD = 0.0;
-    a.bt = INFINITY;
-    a.btf = INFINITY;
-    a.bexc = 0xFFFFFFFFu;
-    a.bpsi = 0.0;
-#pragma unroll
-    for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-        for (int w = 0; w < W; w++) a.bm[sg][w] = n[sg][w];
-}
-
-// rates, local sums and the move race for one neighbour m (Eq. 5, Eq. 16, Sec. II B)
-template <int W, int MODE>
-__device__ __forceinline__ void lane_post(const SysDev& S, LaneAcc<W>& a, const unsigned long long (&m)[2][W],
-                                          double hnm, double hd, bool same_label, double om, double psim,
-                                          double inv_psin, unsigned exc, unsigned step, unsigned wid,
-                                          mrq_neighbour* rec) {
-    const double ratio = psim * inv_psin;
-    const double g = fabs(hnm * ratio);
-    a.sS += g;
-    a.sH += hnm * ratio;
-    if (same_label) a.sHD += hd * ratio;
-    if (MODE == MODE_STEP) {
-        if (g > 0.0) {
-            // exact FP64 clock only where a cheap FP32 bound says it can win
-            const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
-            const float tf = race_clock_f32(k53, (float)g);
-            if (!(tf > a.btf * 1.0001f)) {
-                const double t = race_clock_f64(k53, g);
-                if (t < a.bt || (t == a.bt && exc < a.bexc)) {
-                    a.btf = (float)t;
-                    a.bt = t;
-                    a.bexc = exc;
-                    a.bpsi = psim;
-#pragma unroll
-                    for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-                        for (int w = 0; w < W; w++) a.bm[sg][w] = m[sg][w];
-                }
-            }
-        }
-    } else if (rec != nullptr) {
-#pragma unroll
-        for (int w = 0; w < 4; w++) rec->det[w] = 0;
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-            rec->det[w] = m[0][w];
-            rec->det[W + w] = m[1][w];
-        }
-        rec->h = hnm;
-        rec->hd = same_label ? hd : 0.0;
-        rec->o = om;
-        rec->psi = psim;
-        rec->gamma = g;
-        rec->exc = exc;
-        rec->pad = 0;
-    }
-}
-
-// warp reductions, diagonals, and (MODE_STEP) the winning move
-template <int W, int MODE>
-__device__ LocalOut finish_local(const SysDev& S, const WarpSh& sh, const unsigned long long (&n)[2][W],
-                                 long long ln, int lane, LaneAcc<W>& a, int total,
-                                 unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc) {
-    LocalOut out;
-    out.S = warp_sum(a.sS);
-    const double eh = warp_sum(a.sH);
-    const double ehd = warp_sum(a.sHD);
-    double hnn, hdnn;
-    diagonals<W>(S, sh, n, lane, hnn, hdnn);
-    out.hnn = hnn;
-    out.hdnn = hdnn;
-    out.EL = hnn + eh;
-    out.num = ln > 0 ? hdnn + ehd : 0.0;
-    out.nnb = total;
-    if (MODE == MODE_STEP) {
-        double t = a.bt;
-        unsigned e = a.bexc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double t2 = __shfl_xor_sync(0xffffffffu, t, o);
-            unsigned e2 = __shfl_xor_sync(0xffffffffu, e, o);
-            if (t2 < t || (t2 == t && e2 < e)) {
-                t = t2;
-                e = e2;
-            }
-        }
-        unsigned win = __ballot_sync(0xffffffffu, a.bexc == e && a.bt == t);
-        int src = win ? __ffs(win) - 1 : 0;
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-            for (int w = 0; w < W; w++) best[sg][w] = __shfl_sync(0xffffffffu, a.bm[sg][w], src);
-        best_psi = __shfl_sync(0xffffffffu, a.bpsi, src);
-        best_exc = e;
-    }
-    return out;
-}
-
-// Generic local evaluation at det n (any class) with amplitude psin: one lane per neighbour in
-// the class-block enumeration, reach-back per lane.  MODE_STEP also picks the move; MODE_DEBUG
-// writes neighbour records.  Returns the quantities on every lane.
-template <int W, int MODE, class C>
-__device__ LocalOut local_eval(const SysDev& S, WarpSh& sh, const unsigned long long (&n)[2][W], double psin,
-                               long long ln, int h, int p, unsigned step, unsigned wid, int lane,
-                               unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc,
-                               mrq_neighbour* nbout, long long max_nb, C& ctr) {
-    build_lists<W>(S, n, sh, h, p, lane);
-    const int total = sh.bstart[sh.nb];
-    const double c0 = __ldg(S.c);
-    const double inv_psin = psin != 0.0 ? 1.0 / psin : 0.0;   // zero-amplitude determinants: ratios 0
-    // a CAS walker is itself one reach-back candidate of each of its FOIS neighbours
-    const unsigned long long self_key =
-        ln == 0 ? hash_key(S, active_bits<W>(S, n[0]), active_bits<W>(S, n[1])) : MRQ_EMPTY_KEY;
-    const double phi_self = ln == 0 ? psin / c0 : 0.0;
-    LaneAcc<W> acc;
-    lane_acc_init<W>(acc, n);
-    int b = 0;
-    for (int idx = lane; idx < total; idx += 32) {
-        while (idx >= sh.bstart[b + 1]) b++;
-        const unsigned desc = sh.bdesc[b];
-        int kind, r1, r2, a1, a2;
-        decode_exc(sh, S.n, desc, idx - sh.bstart[b], kind, r1, r2, a1, a2);
-        unsigned long long m[2][W];
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-            for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
-        {
-            int s1 = r1 >= S.n, s2 = a1 >= S.n;
-            flip<W>(m[s1], r1 - s1 * S.n);
-            flip<W>(m[s2], a1 - s2 * S.n);
-            if (kind != 0) {
-                int s3 = r2 >= S.n, s4 = a2 >= S.n;
-                flip<W>(m[s3], r2 - s3 * S.n);
-                flip<W>(m[s4], a2 - s4 * S.n);
-            }
-        }
-        const double hnm =
-            (kind == 0) ? single_elem<W>(S, n, r1, a1, ctr) : double_elem<W>(S, n, r1, r2, a1, a2, ctr);
-        int hm, pm;
-        const long long lm = det_label<W>(S, m, hm, pm);
-        double om, psim;
-        if (lm == 0) {
-            ctr.cand();
-            om = hash_lookup(S, hash_key(S, active_bits<W>(S, m[0]), active_bits<W>(S, m[1])), ctr);
-            psim = c0 * om;
-        } else {
-            om = reach_back<W>(S, m, ctr, self_key, hnm * phi_self);
-            ctr.g();
-            psim = __ldg(S.c + lm) * om;
-        }
-        const bool same = ln > 0 && active_only(desc);
-        const double hd = same ? ((kind == 0) ? hd_single_elem<W>(S, n, r1, a1, ctr) : hnm) : 0.0;
-        const unsigned exc = (unsigned)r1 | ((unsigned)r2 << 8) | ((unsigned)a1 << 16) | ((unsigned)a2 << 24);
-        lane_post<W, MODE>(S, acc, m, hnm, hd, same, om, psim, inv_psin, exc, step, wid,
-                           (MODE == MODE_DEBUG && nbout != nullptr && idx < max_nb) ? nbout + idx : nullptr);
-    }
-    return finish_local<W, MODE>(S, sh, n, ln, lane, acc, total, best, best_psi, best_exc);
-}
-
 #include "mrq_cas.cuh"
-
-#ifndef MRQ_WALK_MIN_BLOCKS
-#define MRQ_WALK_MIN_BLOCKS 3
-#endif
-
-// per-warp shared memory: WarpSh, then the CAS path's candidate list (phi0 values and codes)
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int cap) {
-    const size_t a = (sizeof(WarpSh) + 15) / 16 * 16;
-    return a + (size_t)cap * sizeof(double) + ((size_t)cap * sizeof(unsigned) + 15) / 16 * 16;
-}
-
-__device__ __forceinline__ void warp_smem(unsigned char* base, int cap, WarpSh*& sh, double*& cphi, unsigned*& ccode) {
-    sh = reinterpret_cast<WarpSh*>(base);
-    cphi = reinterpret_cast<double*>(base + (sizeof(WarpSh) + 15) / 16 * 16);
-    ccode = reinterpret_cast<unsigned*>(cphi + cap);
-}
 
 // The walkers of one launch: one or several systems, each with its own walker array; slot numbers
 // run over all systems (system k owns slots [offsets[k], offsets[k+1])).
@@ -488,8 +301,6 @@ struct WalkSet {
     const long long* offsets;
     int nsys;
     long long nslots;
-    double* gscr = nullptr;       // per slot: the CAS walker's single-excitation operator (gstride doubles)
-    long long gstride = 0;
 };
 
 __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, int& sys, long long& local) {
@@ -501,92 +312,6 @@ __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, in
     }
     sys = lo;
     local = slot - ws.offsets[lo];
-}
-
-// One warp per walker slot.  Slot s advances walker order[s] (or s when order is null) by nsteps;
-// ordering the slots by determinant puts walkers that sit on the same determinant into
-// neighbouring warps, which then share cache lines (the results do not depend on the order).
-template <int W>
-__global__ void __launch_bounds__(128, MRQ_WALK_MIN_BLOCKS) k_walk(const WalkSet ws, int nsteps, int cap,
-                                                                   const unsigned* __restrict__ order, int accumulate) {
-    extern __shared__ __align__(16) unsigned char smem_dyn[];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const long long s0 = (long long)blockIdx.x * (blockDim.x >> 5) + wi;
-    if (s0 >= ws.nslots) return;
-    const long long slot = order ? (long long)order[s0] : s0;
-    int sys;
-    long long local;
-    slot_owner(ws, slot, sys, local);
-    Walker* const walkers = ws.walkers[sys];
-    WarpSh* shp;
-    double* cphi;
-    unsigned* ccode;
-    warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
-    WarpSh& sh = *shp;
-    Walker wk = walkers[local];
-    {
-        const int* src = reinterpret_cast<const int*>(ws.systems + sys);
-        int* dst = reinterpret_cast<int*>(&sh.sys);
-        for (int k = lane; k < (int)(sizeof(SysDev) / sizeof(int)); k += 32) dst[k] = src[k];
-        __syncwarp();
-    }
-    const SysDev& S = sh.sys;
-    unsigned long long n[2][W];
-#pragma unroll
-    for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-        for (int w = 0; w < W; w++) n[sg][w] = wk.d[sg][w];
-    double psin = wk.psi;
-    for (int s = 0; s < nsteps; s++) {
-        int h, p;
-        const long long ln = det_label<W>(S, n, h, p);
-        unsigned long long nxt[2][W];
-        double npsi = 0.0;
-        unsigned nexc = 0;
-        NoCtr nc;
-        LocalOut lo;
-        if (ln == 0)
-            lo = local_eval_cas<W, MODE_STEP>(S, sh, cphi, ccode, n, psin, wk.step, wk.wid, lane, nxt, npsi, nexc,
-                                              nullptr, 0, nc, ws.gscr ? ws.gscr + s0 * ws.gstride : nullptr);
-        else {
-            PHASE_T0();
-            lo = local_eval<W, MODE_STEP>(S, sh, n, psin, ln, h, p, wk.step, wk.wid, lane, nxt, npsi, nexc, nullptr,
-                                          0, nc);
-            PHASE_ADD(6);
-        }
-        if (!(lo.S > 0.0) || ln < 0) {
-            if (lane == 0) atomicOr(S.err, ln < 0 ? MRQ_ERR_LABEL : MRQ_ERR_NOMOVE);
-            break;
-        }
-        if (lane == 0 && accumulate && (long long)wk.step >= S.burn_in) {
-            const double w = 1.0 / lo.S;
-            const double cl = __ldg(S.c + ln);
-            const double c2 = cl * cl;
-            const long long base = (long long)wk.group * S.nlab;
-            atomicAdd(S.accN + base + ln, w / c2);
-            if (ln > 0) atomicAdd(S.accU + base + ln, (w * lo.num) / c2);
-            atomicAdd(S.accW + wk.group, w);
-            atomicAdd(S.accE + wk.group, w * lo.EL);
-            atomicAdd(S.accA + base + ln, (w * lo.EL) / cl);
-            atomicAdd(S.accB + base + ln, w / cl);
-            atomicAdd(S.type_steps + 3 * h + p, 1ull);
-        }
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-            for (int w = 0; w < W; w++) n[sg][w] = nxt[sg][w];
-        psin = npsi;
-        wk.step++;
-        __syncwarp();
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-            for (int w = 0; w < W; w++) wk.d[sg][w] = n[sg][w];
-        wk.psi = psin;
-        walkers[local] = wk;
-    }
 }
 
 // sort key of a walker slot: system, label, then the active occupation (truncated), and the slot
@@ -653,84 +378,7 @@ __global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict
     for (int i = threadIdx.x; i < npad; i += blockDim.x) idx[i] = si[i];
 }
 
-// local quantities of arbitrary determinants (parity); CAS determinants take the same grouped
-// path as the walk
-template <int W>
-__global__ void __launch_bounds__(128) k_debug(const SysDev* __restrict__ sys, const unsigned long long* __restrict__ dets,
-                                               long long ndet, mrq_local* __restrict__ out, long long max_nb,
-                                               mrq_neighbour* __restrict__ nb, int cap, double* __restrict__ gscr,
-                                               long long gstride) {
-    extern __shared__ __align__(16) unsigned char smem_dyn[];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const long long i = (long long)blockIdx.x * 4 + wi;
-    if (i >= ndet) return;
-    WarpSh* shp;
-    double* cphi;
-    unsigned* ccode;
-    warp_smem(smem_dyn + wi * warp_smem_bytes(cap), cap, shp, cphi, ccode);
-    WarpSh& sh = *shp;
-    {
-        const int* src = reinterpret_cast<const int*>(sys);
-        int* dst = reinterpret_cast<int*>(&sh.sys);
-        for (int k = lane; k < (int)(sizeof(SysDev) / sizeof(int)); k += 32) dst[k] = src[k];
-        __syncwarp();
-    }
-    const SysDev& S = sh.sys;
-    unsigned long long n[2][W];
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        n[0][w] = dets[i * 2 * W + w];
-        n[1][w] = dets[i * 2 * W + W + w];
-    }
-    int h, p;
-    const long long ln = det_label<W>(S, n, h, p);
-    mrq_local r;
-    memset(&r, 0, sizeof r);
-    r.label = ln;
-    r.type = 3 * h + p;
-    if (ln < 0) {
-        if (lane == 0) out[i] = r;
-        return;
-    }
-    double psin;
-    NoCtr nc0;
-    if (ln == 0) psin = __ldg(S.c) * hash_lookup(S, hash_key(S, active_bits<W>(S, n[0]), active_bits<W>(S, n[1])), nc0);
-    else psin = __ldg(S.c + ln) * reach_back<W>(S, n, nc0);
-    psin = __shfl_sync(0xffffffffu, psin, 0);
-    unsigned long long dummy[2][W];
-    double dpsi;
-    unsigned dexc;
-    Ctr ctr;
-    mrq_neighbour* rec = nb ? nb + i * max_nb : nullptr;
-    LocalOut lo;
-    if (ln == 0 && psin != 0.0)
-        lo = local_eval_cas<W, MODE_DEBUG>(S, sh, cphi, ccode, n, psin, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb,
-                                           ctr, (gscr != nullptr && gstride > 0) ? gscr + i * gstride : nullptr);
-    else
-        lo = local_eval<W, MODE_DEBUG>(S, sh, n, psin, ln, h, p, 0, 0, lane, dummy, dpsi, dexc, rec, max_nb, ctr);
-    unsigned long long cg = ctr.gathers, cp = ctr.probes, cc = ctr.cands, ct = ctr.terms;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cg += __shfl_xor_sync(0xffffffffu, cg, o);
-        cp += __shfl_xor_sync(0xffffffffu, cp, o);
-        cc += __shfl_xor_sync(0xffffffffu, cc, o);
-        ct += __shfl_xor_sync(0xffffffffu, ct, o);
-    }
-    if (lane == 0) {
-        r.n_terms = (long long)ct;
-        r.n_gathers = (long long)cg;
-        r.n_probes = (long long)cp;
-        r.n_candidates = (long long)cc;
-        r.S = lo.S;
-        r.e_local = lo.EL;
-        r.num = lo.num;
-        r.h_nn = lo.hnn;
-        r.hd_nn = lo.hdnn;
-        r.psi = psin;
-        r.n_neighbours = lo.nnb;
-        out[i] = r;
-    }
-}
+#include "mrq_walk.cuh"
 
 __global__ void k_walkers_init(Walker* w, long long nslots, unsigned long long d0, unsigned long long d1,
                                unsigned long long d2, unsigned long long d3, double psi, int sys, int G) {
@@ -743,6 +391,10 @@ __global__ void k_walkers_init(Walker* w, long long nslots, unsigned long long d
     x.wid = (unsigned)i;
     x.sys = sys;
     x.group = (int)(i % G);
+    x.rl = -1;
+    x.rw = x.rEL = x.rnum = 0.0;
+    x.rtype = 0;
+    x.rpad = 0;
     w[i] = x;
 }
 
@@ -1064,6 +716,15 @@ __global__ void k_setup_finish(const SysDev* __restrict__ sys, const double* par
     }
 }
 
+// the race's two clocks for given (k, rate) pairs (parity of the move selection's screen)
+__global__ void k_race_clocks(const unsigned long long* __restrict__ k, const double* __restrict__ rate, long long n,
+                              float* __restrict__ screen, double* __restrict__ exact) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    screen[i] = race_screen(k[i], abs_f32_of(rate[i]));      // as the walk forms it
+    exact[i] = race_clock_f64(k[i], rate[i]);
+}
+
 // index of the largest |c| (first on ties), one block
 __global__ void k_argmax_abs(const double* c, long long n, long long* out) {
     __shared__ double bv[1024];
@@ -1292,6 +953,19 @@ static __device__ __align__(256) double g_noalloc_scratch[MRQ_NOALLOC_SCRATCH_DO
 
 #define MRQ_MAX_DEVICES 64
 static double* g_noalloc_ptr[MRQ_MAX_DEVICES];     // device address of g_noalloc_scratch, per device
+static std::mutex g_noalloc_mu;                    // guards g_noalloc_ptr (contexts may be created concurrently)
+
+// device address of the fixed finalize scratch on `device` (current), looked up once per device
+static double* noalloc_scratch_address(int device) {
+    if (device < 0 || device >= MRQ_MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[device] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess) g_noalloc_ptr[device] = (double*)p;
+        else cudaGetLastError();
+    }
+    return g_noalloc_ptr[device];
+}
 
 // ============================================================================ host runtime
 
@@ -1307,6 +981,7 @@ struct mrq_ctx {
     long long neri = 0;
     double *d_h1 = nullptr, *d_eri = nullptr, *d_eri4 = nullptr, *d_tab = nullptr, *d_hc = nullptr,
            *d_eps = nullptr, *d_gamma = nullptr;
+    unsigned short* d_colex = nullptr;
     long long nHs = 0, nPs = 0, nlab = 0;
     // reference
     bool ref = false;
@@ -1353,23 +1028,23 @@ struct mrq_ctx {
     SysDev* d_sys = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch configuration (mrq_set_launch, mrq_tune_batch)
-    int wpb = 4;                     // walkers (warps) per block
+    int wpb = 0;                     // warps per walker block (0: chosen from the system's work units)
     int spl = 0;                     // steps per launch (0: every advance is one launch)
     int use_graph = 0;               // batches replay one reporting interval from a CUDA graph
     struct GraphKey {
-        const void *sys = nullptr, *wptr = nullptr, *off = nullptr, *keys = nullptr, *gscr = nullptr;
+        const void *sys = nullptr, *wptr = nullptr, *off = nullptr, *keys = nullptr;
         long long nslots = 0;
-        int k = 0, wpb = 0, spl = 0, cap = 0;
+        int k = 0, wpb = 0, spl = 0, cap = 0, gstride = 0;
         bool operator==(const GraphKey& o) const {
-            return sys == o.sys && wptr == o.wptr && off == o.off && keys == o.keys && gscr == o.gscr && nslots == o.nslots &&
-                   k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap;
+            return sys == o.sys && wptr == o.wptr && off == o.off && keys == o.keys && nslots == o.nslots &&
+                   k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap && gstride == o.gstride;
         }
     };
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // per determinant width
     GraphKey gkey[2];
     long long graph_replays = 0;
-    double* d_gscr = nullptr;        // per walk slot: a CAS walker's single-excitation operator
-    long long gscr_cap = 0;
+    long long* d_nbpre = nullptr;    // debug records: neighbour offsets of a determinant's units
+    long long nbpre_cap = 0;
     Walker* d_tune = nullptr;        // the tuner's scratch copy of a batch's walkers
     long long tune_cap = 0;
     Walker** d_tptr = nullptr;
@@ -1379,6 +1054,13 @@ struct mrq_ctx {
     long long launches_total = 0;
     double walk_ms = 0.0;
     long long total_steps = 0;
+    // failure detection: host-wait deadline and lowered device bounds (mrq_set_deadline,
+    // mrq_debug_set_limits)
+    double deadline_s = 0.0;         // 0: host waits have no deadline
+    cudaEvent_t ev_wait = nullptr;
+    int probe_limit = 0, cap_limit = 0;
+    int cand_cap_full = 1;           // the candidate-list capacity the loaded system needs
+    double l2_fraction = 0.0;        // mrq_set_l2_window: share of the persisting-L2 carve-out for the tables
 };
 
 static int fail(mrq_ctx* c, int code, const char* fmt, ...) {
@@ -1398,6 +1080,38 @@ static int fail(mrq_ctx* c, int code, const char* fmt, ...) {
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? MRQ_OOM : MRQ_CUDA_ERROR, "%s: %s (%s:%d)", \
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
     } while (0)
+
+// Wait for the context stream.  With a deadline set (mrq_set_deadline) the wait polls an event
+// and gives up with MRQ_DEVICE_TIMEOUT once the deadline passes; the device work keeps running
+// and the next wait on this context waits for it again.
+static int sync_stream(mrq_ctx* ctx) {
+    if (!(ctx->deadline_s > 0.0) || ctx->ev_wait == nullptr) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return 0;
+    }
+    CK(cudaEventRecord(ctx->ev_wait, ctx->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ctx->ev_wait);
+        if (e == cudaSuccess) return 0;
+        if (e != cudaErrorNotReady) return fail(ctx, MRQ_CUDA_ERROR, "cudaEventQuery: %s", cudaGetErrorString(e));
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > ctx->deadline_s)
+            return fail(ctx, MRQ_DEVICE_TIMEOUT,
+                        "device work did not finish within the %.6f s deadline; it keeps running and the next "
+                        "call on this context waits for it", ctx->deadline_s);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Set-up calls wait for earlier work under the deadline, then run their own kernels and copies to
+// the end without one (so a timeout never leaves a half-built table or a temporary buffer behind).
+struct DeadlinePause {
+    mrq_ctx* c;
+    double d;
+    explicit DeadlinePause(mrq_ctx* ctx) : c(ctx), d(ctx->deadline_s) { ctx->deadline_s = 0.0; }
+    ~DeadlinePause() { c->deadline_s = d; }
+};
 
 template <typename T>
 static void dfree(T*& p) {
@@ -1437,6 +1151,7 @@ static void free_hamiltonian(mrq_ctx* c) {
     dfree(c->d_hc);
     dfree(c->d_eps);
     dfree(c->d_gamma);
+    dfree(c->d_colex);
     c->ham = false;
 }
 
@@ -1459,14 +1174,17 @@ static int push_sys(mrq_ctx* ctx) {
     s.e0 = ctx->e0;
     s.e_core = ctx->e_core;
     s.sum_eps_core = ctx->sum_eps_core;
+    s.max_probe = ctx->probe_limit > 0 ? std::min(64, ctx->probe_limit) : 64;
+    s.cand_cap = ctx->cap_limit > 0 ? std::min(ctx->cand_cap_full, ctx->cap_limit) : ctx->cand_cap_full;
     CK(cudaMemcpyAsync(ctx->d_sys, &s, sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
     return 0;
 }
 
 static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
     int f = 0;
+    if (int r = sync_stream(ctx)) return r;
     CK(cudaMemcpyAsync(&f, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));    // idle already: returns at once
     *flag_out = f;
     return 0;
 }
@@ -1474,9 +1192,10 @@ static int check_err_flag(mrq_ctx* ctx, int* flag_out) {
 // launch-time options of a walk: warps (walkers) per block, whether to accumulate, and whether the
 // one-time set-up (buffer growth, function attributes) has been done already (inside a stream capture)
 struct WalkLaunch {
-    int wpb = 4;
+    int wpb = 8;
     int accumulate = 1;
     bool captured = false;
+    cudaAccessPolicyWindow l2win = {};   // num_bytes 0: no persisting-L2 window
 };
 
 static int walk_sort_prepare(mrq_ctx* ctx, long long nslots) {
@@ -1495,60 +1214,182 @@ static int walk_sort_prepare(mrq_ctx* ctx, long long nslots) {
     return 0;
 }
 
-#ifndef MRQ_WALK_CARVEOUT
-#define MRQ_WALK_CARVEOUT -1     // preferred shared-memory carveout of k_walk in percent (-1: driver default)
-#endif
-
-// the walk set's per-slot scratch of the CAS walkers' single-excitation operators
-static int walk_gscr_prepare(mrq_ctx* ctx, long long doubles) {
-    if (doubles > ctx->gscr_cap) {
-        dfree(ctx->d_gscr);
-        CK(cudaMalloc(&ctx->d_gscr, sizeof(double) * doubles));
-        ctx->gscr_cap = doubles;
-    }
+static int walk_attr_prepare(mrq_ctx* ctx, int W, size_t smem) {
+    if (W == 1) CK(cudaFuncSetAttribute(k_walk2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else CK(cudaFuncSetAttribute(k_walk2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return 0;
 }
 
-static int walk_attr_prepare(mrq_ctx* ctx, int W, int wpb, int cap) {
-    const int smem = (int)(wpb * warp_smem_bytes(cap));
-    if (W == 1) CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    else CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    if (MRQ_WALK_CARVEOUT >= 0) {
-        if (W == 1) CK(cudaFuncSetAttribute(k_walk<1>, cudaFuncAttributePreferredSharedMemoryCarveout, MRQ_WALK_CARVEOUT));
-        else CK(cudaFuncSetAttribute(k_walk<2>, cudaFuncAttributePreferredSharedMemoryCarveout, MRQ_WALK_CARVEOUT));
-    }
-    return 0;
+// warps per walker block when the caller leaves the choice to the library: enough warps to share a
+// CAS walker's work units, fewer for small systems whose units would leave warps idle
+static int auto_warps(const SysDev& s) {
+    const int u = s.unit_off[8];
+    return u >= 512 ? 8 : (u >= 128 ? 4 : 2);
 }
+static int warps_of(const mrq_ctx* ctx) { return ctx->wpb > 0 ? ctx->wpb : auto_warps(ctx->hsys); }
 
-// walk launch: order the slots by determinant (when the slot count allows a one-block sort),
-// then one warp per slot; `ctx` provides the stream and the sort scratch
-static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws_in, int nsteps, int cap, const WalkLaunch& L = WalkLaunch()) {
-    const int wpb = L.wpb;
-    const size_t smem = wpb * warp_smem_bytes(cap);
-    const unsigned* order = nullptr;
-    const long long nslots = ws_in.nslots;
+// nsteps walker steps of a walk set: per step, order the slots by determinant (when the slot count
+// allows a one-block sort), one block of L.wpb warps per walker slot (k_walk2), then the
+// deterministic accumulation of the step's records (k_accum); `ctx` provides the stream and the
+// sort scratch.  cap / gstride: the largest candidate-list capacity and single-operator size of
+// the set's systems.
+static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int cap, int gstride,
+                       const WalkLaunch& L = WalkLaunch()) {
+    const int nw = std::min(L.wpb, MRQ_MAXNW);
+    const size_t smem = cta_smem_bytes(nw, cap, gstride);
+    const long long nslots = ws.nslots;
     if (!L.captured) {
         if (int r = walk_sort_prepare(ctx, nslots)) return r;
-        if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
-        if (int r = walk_gscr_prepare(ctx, nslots * ws_in.gstride)) return r;
+        if (int r = walk_attr_prepare(ctx, W, smem)) return r;
     }
-    WalkSet ws = ws_in;
-    ws.gscr = ws.gstride > 0 ? ctx->d_gscr : nullptr;
-    if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
-        long long npad = 1;
-        while (npad < nslots) npad <<= 1;
-        const unsigned nb = (unsigned)((npad + 255) / 256);
-        if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
-        else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
-        const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
-        k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
-        CK(cudaGetLastError());
-        order = ctx->d_sort_idx;
+    for (int step = 0; step < nsteps; step++) {
+        const unsigned* order = nullptr;
+        if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
+            long long npad = 1;
+            while (npad < nslots) npad <<= 1;
+            const unsigned nb = (unsigned)((npad + 255) / 256);
+            if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+            else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
+            const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
+            k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
+            CK(cudaGetLastError());
+            order = ctx->d_sort_idx;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)nslots);
+        cfg.blockDim = dim3(32 * nw);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        if (L.l2win.num_bytes > 0) {            // keep the walk's hottest table resident in L2
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+            attr[0].val.accessPolicyWindow = L.l2win;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+        }
+        if (W == 1) CK(cudaLaunchKernelEx(&cfg, k_walk2<1>, ws, order, L.accumulate));
+        else CK(cudaLaunchKernelEx(&cfg, k_walk2<2>, ws, order, L.accumulate));
+        if (L.accumulate) {
+            k_accum<<<dim3((unsigned)ws.nsys, 2), 1024, 0, ctx->stream>>>(ws);
+            CK(cudaGetLastError());
+        }
     }
-    const unsigned blocks = (unsigned)((nslots + wpb - 1) / wpb);
-    if (W == 1) k_walk<1><<<blocks, 32 * wpb, smem, ctx->stream>>>(ws, nsteps, cap, order, L.accumulate);
-    else k_walk<2><<<blocks, 32 * wpb, smem, ctx->stream>>>(ws, nsteps, cap, order, L.accumulate);
-    CK(cudaGetLastError());
+    return 0;
+}
+
+// ---------------------------------------------------------------- work plan of the walk (host)
+
+static long long nsub_h(long long k, int size) {
+    if (size < 0 || k < size) return 0;
+    return size == 0 ? 1 : (size == 1 ? k : k * (k - 1) / 2);
+}
+static long long shape_h(long long m, int cnt, int nal) {
+    if (cnt == 0) return 1;
+    if (cnt == 1) return m;
+    return nal == 1 ? m * m : m * (m - 1) / 2;
+}
+// neighbours of one (X_a, Y_a) pair of a CAS walker with alpha(Y_a) - alpha(X_a) = d
+static long long pair_total_h(int nc, int nv, int ka, int kb, int d) {
+    long long tot = 0;
+    for (int r = std::max(1, std::max(ka, kb)); r <= 2; r++) {
+        const int c = r - ka, v = r - kb;
+        if (c == 0 && v == 0) continue;
+        for (int sc = 0; sc <= c; sc++) {
+            const int sv = sc - d;
+            if (sv < 0 || sv > v) continue;
+            tot += shape_h(nc, c, sc) * shape_h(nv, v, sv);
+        }
+    }
+    return tot;
+}
+
+// The CAS walkers' work units (the same for every CAS determinant: all hold n_alpha - n_core alpha
+// and n_beta - n_core beta active electrons), the largest candidate list of a group (spin-resolved:
+// the alpha count of R' fixes that of A'), and the walk block's shared memory.
+static int walk_plan(mrq_ctx* ctx, SysDev& s) {
+    const int nc = s.nc, na = s.na, nv = s.nv;
+    const int nao = s.nalpha - nc, nbo = s.nbeta - nc, cea = na - nao, ceb = na - nbo;
+    const int cntO = nao + nbo, cntE = cea + ceb;
+    long long cas_nb = nao * (long long)cea + nbo * (long long)ceb + nsub_h(nao, 2) * nsub_h(cea, 2) +
+                       nsub_h(nbo, 2) * nsub_h(ceb, 2) + (long long)nao * cea * nbo * ceb;
+    long long total = cas_nb;
+    long long off = (cas_nb + MRQ_CAS_CH - 1) / MRQ_CAS_CH;
+    s.cas_nb = (int)cas_nb;
+    s.cas_units = (int)off;
+    for (int k = 0; k < 8; k++) {
+        const int ka = k / 3, kb = k % 3;
+        const long long npairs = nsub_h(cntO, ka) * nsub_h(cntE, kb);
+        long long maxN = 0;
+        for (int xal = 0; xal <= ka; xal++)
+            for (int yal = 0; yal <= kb; yal++) {
+                const long long nx = nsub_h(nao, xal) * nsub_h(nbo, ka - xal);
+                const long long ny = nsub_h(cea, yal) * nsub_h(ceb, kb - yal);
+                if (nx == 0 || ny == 0) continue;
+                const long long N = pair_total_h(nc, nv, ka, kb, yal - xal);
+                total += nx * ny * N;
+                maxN = std::max(maxN, N);
+            }
+        const long long nch = std::max(1LL, (maxN + MRQ_UNIT_NB - 1) / MRQ_UNIT_NB);
+        s.nch[k] = (int)nch;
+        s.unit_off[k] = (int)off;
+        off += npairs * nch;
+    }
+    s.unit_off[8] = (int)off;
+    s.cas_nb_total = total;
+    if (off > (1LL << 30) || total > (1LL << 40))
+        return fail(ctx, MRQ_TOO_LARGE, "active space too large for the walk's work plan");
+    // largest candidate list: m's active occupation differs from n's by at most two electrons
+    long long cap = 1;
+    for (int oa = std::max(0, nao - 2); oa <= std::min(na, nao + 2); oa++)
+        for (int ob = std::max(0, nbo - 2); ob <= std::min(na, nbo + 2); ob++) {
+            if (std::abs(oa + ob - cntO) > 2) continue;
+            const int ea = na - oa, eb = na - ob;
+            for (int c = 0; c <= 2; c++)
+                for (int v = 0; v <= 2; v++) {
+                    if (c == 0 && v == 0) continue;
+                    for (int sc = 0; sc <= c; sc++)
+                        for (int sv = 0; sv <= v; sv++) {
+                            long long t = 0;
+                            for (int rr = 1; rr <= 2; rr++) {
+                                if (rr == 1 && (c > 1 || v > 1)) continue;
+                                const int ne = rr - v, nf = rr - c;
+                                if (ne < 0 || nf < 0) continue;
+                                for (int i = 0; i <= ne; i++) {
+                                    const int j = i + sv - sc;
+                                    if (j < 0 || j > nf) continue;
+                                    t += nsub_h(oa, i) * nsub_h(ob, ne - i) * nsub_h(ea, j) * nsub_h(eb, nf - j);
+                                }
+                            }
+                            cap = std::max(cap, t);
+                        }
+                }
+        }
+    s.gstride = 2 * s.nca * s.nav;
+    s.cand_cap = (int)cap;
+    ctx->cand_cap_full = (int)cap;
+    if (cta_smem_bytes(MRQ_MAXNW, (int)cap, s.gstride) > 227 * 1024)
+        return fail(ctx, MRQ_TOO_LARGE, "active space too large for the shared-memory candidate lists");
+    return 0;
+}
+
+// The persisting-L2 window of a walk launch (mrq_set_l2_window): the physicists' tables, which
+// every reach-back term reads, marked persisting up to the device's carve-out (the carve-out is a
+// per-process limit of this CUDA context and ends with it).
+static int l2_window(mrq_ctx* ctx, cudaAccessPolicyWindow& w) {
+    w = cudaAccessPolicyWindow{};
+    if (!(ctx->l2_fraction > 0.0) || !ctx->d_tab) return 0;
+    int maxwin = 0, maxpersist = 0;
+    CK(cudaDeviceGetAttribute(&maxwin, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
+    CK(cudaDeviceGetAttribute(&maxpersist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
+    if (maxwin <= 0 || maxpersist <= 0) return 0;
+    const size_t tab_bytes = sizeof(double) * 2 * (size_t)ctx->hsys.tab_half;
+    const size_t carve = (size_t)(ctx->l2_fraction * (double)maxpersist);
+    CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, carve));
+    w.base_ptr = ctx->d_tab;
+    w.num_bytes = std::min(tab_bytes, (size_t)maxwin);
+    w.hitRatio = (float)std::min(1.0, (double)carve / (double)w.num_bytes);
+    w.hitProp = cudaAccessPropertyPersisting;
+    w.missProp = cudaAccessPropertyStreaming;
     return 0;
 }
 
@@ -1567,7 +1408,8 @@ int mrq_create(mrq_ctx** out, int device) {
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMalloc(&ctx->d_sys, sizeof(SysDev)) != cudaSuccess ||
         cudaMalloc(&ctx->d_res, sizeof(mrq_result)) != cudaSuccess || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
-        cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_wait, cudaEventDisableTiming) != cudaSuccess) {
         mrq_destroy(ctx);
         return MRQ_CUDA_ERROR;
     }
@@ -1575,11 +1417,7 @@ int mrq_create(mrq_ctx** out, int device) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     // set-up of the allocation-free finalize: the device address of the fixed scratch array,
     // looked up once per device with that device current (host code cannot use the symbol itself)
-    if (device >= 0 && device < MRQ_MAX_DEVICES && g_noalloc_ptr[device] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess) g_noalloc_ptr[device] = (double*)p;
-        else cudaGetLastError();
-    }
+    noalloc_scratch_address(device);
     *out = ctx;
     return 0;
 }
@@ -1603,12 +1441,13 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_boff);
     dfree(ctx->d_tune);
     dfree(ctx->d_tptr);
-    dfree(ctx->d_gscr);
+    dfree(ctx->d_nbpre);
     for (int w = 0; w < 2; w++)
         if (ctx->gexec[w]) cudaGraphExecDestroy(ctx->gexec[w]);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -1618,7 +1457,7 @@ const char* mrq_last_error(const mrq_ctx* ctx) { return ctx ? ctx->err : "null c
 int mrq_set_stream(mrq_ctx* ctx, void* stream) {
     if (!ctx) return MRQ_INVALID_ARG;
     CK(cudaSetDevice(ctx->device));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     if (stream) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         ctx->stream = (cudaStream_t)stream;
@@ -1643,7 +1482,8 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     if (n_alpha < n_core || n_beta < n_core || n_alpha > n_core + n_act || n_beta > n_core + n_act)
         return fail(ctx, MRQ_INVALID_ARG, "electron counts must fill the core and fit the active space");
     CK(cudaSetDevice(ctx->device));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
+    DeadlinePause pause_(ctx);
     free_walkers(ctx);
     free_reference(ctx);
     free_hamiltonian(ctx);
@@ -1668,6 +1508,16 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     CK(cudaMalloc(&ctx->d_hc, sizeof(double) * n * n));
     CK(cudaMalloc(&ctx->d_eps, sizeof(double) * n));
     CK(cudaMalloc(&ctx->d_gamma, sizeof(double) * std::max(1, n_act * n_act)));
+    {
+        // co-lexicographic pair table of up to 128 items: colex[j(j-1)/2 + i] = i | j << 8, i < j
+        std::vector<unsigned short> colex(128 * 127 / 2);
+        for (int j = 1, q = 0; j < 128; j++)
+            for (int i = 0; i < j; i++) colex[q++] = (unsigned short)(i | (j << 8));
+        CK(cudaMalloc(&ctx->d_colex, sizeof(unsigned short) * colex.size()));
+        CK(cudaMemcpyAsync(ctx->d_colex, colex.data(), sizeof(unsigned short) * colex.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     CK(cudaMemcpyAsync(ctx->d_h1, h1, sizeof(double) * n * n, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d_eri, eri, sizeof(double) * ctx->neri, cudaMemcpyDefault, ctx->stream));
     SysDev& s = ctx->hsys;
@@ -1696,30 +1546,16 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     s.nca = (int)nca;
     s.nav = (int)nav;
     s.tab_half = (unsigned)(nca * nca * nav * nav);
+    s.colex = ctx->d_colex;
+    s.mag_c = n_core > 1 ? ~0ull / (unsigned long long)n_core + 1ull : 0ull;
+    s.mag_v = n_virt > 1 ? ~0ull / (unsigned long long)n_virt + 1ull : 0ull;
     s.h1 = ctx->d_h1;
     s.hc = ctx->d_hc;
     s.eps = ctx->d_eps;
     s.e_nuc = e_core;
     s.max_probe = 64;
     s.G = 1;
-    {
-        // largest candidate list of one group of the CAS path: |R'| = rr - p active electrons and
-        // |A'| = rr - h active holes of a remnant with at most N_act + 2 electrons / holes
-        auto nsub_h = [](long long k, int size) { return size == 0 ? 1LL : (size == 1 ? k : k * (k - 1) / 2); };
-        const int nact_e = (n_alpha - n_core) + (n_beta - n_core);
-        const long long amax = std::min(2 * n_act, nact_e + 2), emax = std::min(2 * n_act, 2 * n_act - nact_e + 2);
-        long long cap = 1;
-        for (int hc = 0; hc <= 2; hc++)
-            for (int pc = 0; pc <= 2; pc++) {
-                if (hc == 0 && pc == 0) continue;
-                long long t = nsub_h(amax, 2 - pc) * nsub_h(emax, 2 - hc);
-                if (hc <= 1 && pc <= 1) t += nsub_h(amax, 1 - pc) * nsub_h(emax, 1 - hc);
-                cap = std::max(cap, t);
-            }
-        s.cand_cap = (int)cap;
-        if (4 * warp_smem_bytes(s.cand_cap) > 200 * 1024)
-            return fail(ctx, MRQ_TOO_LARGE, "active space too large for the shared-memory candidate lists");
-    }
+    if (int r = walk_plan(ctx, s)) return r;
     if (int r = push_sys(ctx)) return r;
     k_expand_eri<<<1216, 256, 0, ctx->stream>>>(ctx->d_eri, ctx->d_eri4, n);
     CK(cudaGetLastError());
@@ -1727,7 +1563,7 @@ int mrq_load_hamiltonian(mrq_ctx* ctx, int n_core, int n_act, int n_virt, int n_
     CK(cudaGetLastError());
     k_core_fock<<<(n * n + 127) / 128, 128, 0, ctx->stream>>>(ctx->d_sys, ctx->d_hc);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     ctx->ham = true;
     return 0;
 }
@@ -1738,7 +1574,8 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
     if (!ctx->ham) return fail(ctx, MRQ_NOT_LOADED, "load the Hamiltonian first");
     if (n_det <= 0 || !dets || !coeffs) return fail(ctx, MRQ_INVALID_ARG, "empty reference");
     CK(cudaSetDevice(ctx->device));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
+    DeadlinePause pause_(ctx);
     free_walkers(ctx);
     free_reference(ctx);
     const int W = ctx->W;
@@ -1758,7 +1595,7 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
         std::vector<double> c(ctx->nlab, 0.1);
         c[0] = 1.0;
         CK(cudaMemcpyAsync(ctx->d_c, c.data(), sizeof(double) * ctx->nlab, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        if (int r_ = sync_stream(ctx)) return r_;
     }
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     if (int r = push_sys(ctx)) return r;
@@ -1782,7 +1619,7 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
     CK(cudaMalloc(&d_idx, sizeof(long long)));
     k_argmax_abs<<<1, 1024, 0, ctx->stream>>>(d_co, n_det, d_idx);
     CK(cudaMemcpyAsync(&ctx->start_idx, d_idx, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     cudaFree(d_idx);
     memset(ctx->start, 0, sizeof ctx->start);
     {
@@ -1818,7 +1655,7 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
     if (ctx->na)
         CK(cudaMemcpyAsync(ctx->gamma.data(), ctx->d_gamma, sizeof(double) * ctx->na * ctx->na, cudaMemcpyDeviceToHost,
                            ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     cudaFree(d_part);
     cudaFree(d_scal);
     cudaFree(d_dets);
@@ -1831,7 +1668,7 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
     if (int r = check_err_flag(ctx, &flag2)) return r;
     if (flag2 & MRQ_ERR_HASH) return fail(ctx, MRQ_HASH_OVERFLOW, "hash probe bound exceeded during setup");
     if (int r = push_sys(ctx)) return r;
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     ctx->ref = true;
     return 0;
 }
@@ -1847,7 +1684,7 @@ int mrq_set_coeffs(mrq_ctx* ctx, int64_t n_labels, const double* c) {
     dfree(ctx->d_am_v);
     dfree(ctx->d_am_vh);
     CK(cudaMemcpyAsync(ctx->d_c, c, sizeof(double) * n_labels, cudaMemcpyDefault, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     return 0;
 }
 
@@ -1871,6 +1708,7 @@ int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* lo
     if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
     if (n <= 0 || !dets || !local || (nb && max_nb <= 0)) return fail(ctx, MRQ_INVALID_ARG, "bad arguments");
     CK(cudaSetDevice(ctx->device));
+    DeadlinePause pause_(ctx);
     const int W = ctx->W;
     unsigned long long* d_dets = nullptr;
     mrq_local* d_loc = nullptr;
@@ -1881,21 +1719,28 @@ int mrq_debug_local(mrq_ctx* ctx, int64_t n, const uint64_t* dets, mrq_local* lo
     CK(cudaMemcpyAsync(d_dets, dets, sizeof(unsigned long long) * 2 * W * n, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     if (int r = push_sys(ctx)) return r;
-    const unsigned blocks = (unsigned)((n + 3) / 4);
     const int cap = ctx->hsys.cand_cap;
-    const size_t smem = 4 * warp_smem_bytes(cap);
-    const long long gstride = 2LL * ctx->hsys.nca * ctx->hsys.nav;
-    if (int r = walk_gscr_prepare(ctx, n * gstride)) return r;
+    const int nw = std::min(warps_of(ctx), MRQ_MAXNW);
+    const size_t smem = cta_smem_bytes(nw, cap, ctx->hsys.gstride);
+    // neighbour offsets of the CAS units, for the records
+    const long long stride = nb ? std::max(1, ctx->hsys.unit_off[8]) : 0;
+    if (nb && n * stride > ctx->nbpre_cap) {
+        dfree(ctx->d_nbpre);
+        CK(cudaMalloc(&ctx->d_nbpre, sizeof(long long) * n * stride));
+        ctx->nbpre_cap = n * stride;
+    }
+    long long* pre = nb ? ctx->d_nbpre : nullptr;
     if (W == 1) {
-        CK(cudaFuncSetAttribute(k_debug<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_debug<1><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap, ctx->d_gscr,
-                                                       gstride);
+        CK(cudaFuncSetAttribute(k_debug2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_debug2<1><<<(unsigned)n, 32 * nw, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, pre,
+                                                                 (int)stride);
     } else {
-        CK(cudaFuncSetAttribute(k_debug<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_debug<2><<<blocks, 128, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, cap, ctx->d_gscr,
-                                                       gstride);
+        CK(cudaFuncSetAttribute(k_debug2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_debug2<2><<<(unsigned)n, 32 * nw, smem, ctx->stream>>>(ctx->d_sys, d_dets, n, d_loc, max_nb, d_nb, pre,
+                                                                 (int)stride);
     }
     CK(cudaGetLastError());
+    if (int r = sync_stream(ctx)) return r;
     CK(cudaMemcpyAsync(local, d_loc, sizeof(mrq_local) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (nb) CK(cudaMemcpyAsync(nb, d_nb, sizeof(mrq_neighbour) * n * max_nb, cudaMemcpyDeviceToHost, ctx->stream));
     int flag = 0;
@@ -1914,12 +1759,14 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
     if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
     if (p->n_walkers <= 0 || p->n_groups <= 0 || p->n_groups > 64 || p->n_steps < 0 || p->burn_in < 0)
         return fail(ctx, MRQ_INVALID_ARG, "need n_walkers > 0, 1 <= n_groups <= 64, n_steps >= 0, burn_in >= 0");
-    if (p->walkers_per_block != 0 && p->walkers_per_block != 1 && p->walkers_per_block != 2 && p->walkers_per_block != 4)
-        return fail(ctx, MRQ_INVALID_ARG, "walkers_per_block must be 0, 1, 2 or 4");
+    if (p->warps_per_walker != 0 && p->warps_per_walker != 1 && p->warps_per_walker != 2 && p->warps_per_walker != 4 &&
+        p->warps_per_walker != 8)
+        return fail(ctx, MRQ_INVALID_ARG, "warps_per_walker must be 0, 1, 2, 4 or 8");
     if (p->steps_per_check < 0 || p->target_sigma < 0.0)
         return fail(ctx, MRQ_INVALID_ARG, "need steps_per_check >= 0 and target_sigma >= 0");
-    if (p->walkers_per_block) ctx->wpb = p->walkers_per_block;
+    if (p->warps_per_walker) ctx->wpb = p->warps_per_walker;
     CK(cudaSetDevice(ctx->device));
+    DeadlinePause pause_(ctx);
     if (p->n_walkers > ctx->walk_cap) {
         dfree(ctx->d_walk);
         CK(cudaMalloc(&ctx->d_walk, sizeof(Walker) * p->n_walkers));
@@ -1963,7 +1810,7 @@ int mrq_walkers_init(mrq_ctx* ctx, const mrq_sample_params* p) {
     if (int r = push_sys(ctx)) return r;
     double c0 = 1.0;
     CK(cudaMemcpyAsync(&c0, ctx->d_c, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     if (!ctx->d_wptr) {
         CK(cudaMalloc(&ctx->d_wptr, sizeof(Walker*)));
         CK(cudaMalloc(&ctx->d_woff, 2 * sizeof(long long)));
@@ -1994,12 +1841,13 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
     WalkSet ws{ctx->d_sys, ctx->d_wptr, ctx->d_woff, 1, ctx->nwalk};
-    ws.gstride = 2LL * ctx->hsys.nca * ctx->hsys.nav;
     WalkLaunch L;
-    L.wpb = ctx->wpb;
+    L.wpb = warps_of(ctx);
+    if (int r = l2_window(ctx, L.l2win)) return r;
     const int64_t spl = ctx->spl > 0 ? ctx->spl : n_steps;
     for (int64_t done = 0; done < n_steps; done += spl)
-        if (int r = launch_walk(ctx, ctx->W, ws, (int)std::min<int64_t>(spl, n_steps - done), ctx->hsys.cand_cap, L))
+        if (int r = launch_walk(ctx, ctx->W, ws, (int)std::min<int64_t>(spl, n_steps - done), ctx->hsys.cand_cap,
+                                ctx->hsys.gstride, L))
             return r;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->evs[k + 1], ctx->stream));
@@ -2016,13 +1864,14 @@ static long long fin_scratch_doubles(const mrq_ctx* ctx, int* nchunk) {
 }
 
 // finalize with the partial sums in `scratch` (at least fin_scratch_doubles() doubles)
+// (the device copy of the system is current since mrq_walkers_init pushed it, so nothing is copied
+// in: a copy from pageable host memory would wait for the walk and defeat the deadline)
 static int finalize_with(mrq_ctx* ctx, mrq_result* out, double* scratch, int nchunk) {
-    ctx->hsys.e0 = ctx->e0;
-    if (int r = push_sys(ctx)) return r;
     k_fin_labels<<<(ctx->G + 1) * nchunk, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->tau, nchunk, FIN_CHUNK, scratch);
     CK(cudaGetLastError());
     k_fin_reduce<<<1, 256, 0, ctx->stream>>>(ctx->d_sys, scratch, nchunk, ctx->d_res);
     CK(cudaGetLastError());
+    if (int r = sync_stream(ctx)) return r;
     CK(cudaMemcpyAsync(out, ctx->d_res, sizeof(mrq_result), cudaMemcpyDeviceToHost, ctx->stream));
     int flag = 0;
     if (int r = check_err_flag(ctx, &flag)) return r;
@@ -2060,7 +1909,12 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
     if (!ctx || !out) return MRQ_INVALID_ARG;
     ctx->err[0] = 0;
     if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
-    if (ctx->device < 0 || ctx->device >= MRQ_MAX_DEVICES || g_noalloc_ptr[ctx->device] == nullptr)
+    double* scratch = nullptr;
+    if (ctx->device >= 0 && ctx->device < MRQ_MAX_DEVICES) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        scratch = g_noalloc_ptr[ctx->device];
+    }
+    if (scratch == nullptr)
         return fail(ctx, MRQ_CUDA_ERROR, "fixed finalize scratch has no device address on device %d", ctx->device);
     int nchunk = 0;
     const long long need = fin_scratch_doubles(ctx, &nchunk);
@@ -2069,7 +1923,7 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
                     "mrq_finalize_noalloc: %lld labels x %d groups need %lld scratch doubles, more than its fixed "
                     "%d (use mrq_finalize)", (long long)ctx->nlab, ctx->G, need, MRQ_NOALLOC_SCRATCH_DOUBLES);
     CK(cudaSetDevice(ctx->device));
-    return finalize_with(ctx, out, g_noalloc_ptr[ctx->device], nchunk);
+    return finalize_with(ctx, out, scratch, nchunk);
 }
 
 int mrq_mrci_gradient(mrq_ctx* ctx, double* grad, double* energy) {
@@ -2085,7 +1939,7 @@ int mrq_mrci_gradient(mrq_ctx* ctx, double* grad, double* energy) {
     double e = 0.0;
     if (grad) CK(cudaMemcpyAsync(grad, ctx->d_grad, sizeof(double) * ctx->nlab, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemcpyAsync(&e, ctx->d_grad + ctx->nlab, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     if (energy) *energy = e;
     return 0;
 }
@@ -2108,7 +1962,7 @@ int mrq_amsgrad_step(mrq_ctx* ctx, double lr, double beta1, double beta2, double
     k_amsgrad<<<(unsigned)std::min<long long>(1024, (ctx->nlab + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->d_c, ctx->d_grad, ctx->d_am_m, ctx->d_am_v, ctx->d_am_vh, ctx->nlab, lr, beta1, beta2, eps);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     return 0;
 }
 
@@ -2116,8 +1970,9 @@ int mrq_read_coeffs(mrq_ctx* ctx, double* c) {
     if (!ctx || !c) return MRQ_INVALID_ARG;
     if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
     CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
     CK(cudaMemcpyAsync(c, ctx->d_c, sizeof(double) * ctx->nlab, cudaMemcpyDefault, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     return 0;
 }
 
@@ -2139,7 +1994,8 @@ static int batch_check(mrq_ctx* const* ctxs, int n) {
 
 // the batch's systems of determinant width W: device tables in the lead context, walker arrays
 // from `walkers` (the contexts' own, or the tuner's scratch copies)
-static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walkers, WalkSet& ws, int& cap) {
+static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walkers, WalkSet& ws, int& cap,
+                        int& gstride) {
     mrq_ctx* ctx = ctxs[0];
     if (n > ctx->bcap) {
         dfree(ctx->d_bsys);
@@ -2162,7 +2018,8 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
         cap = std::max(cap, ctxs[i]->hsys.cand_cap);
     }
     ws = WalkSet{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, (int)sys.size(), off.back()};
-    for (const SysDev& sd : sys) ws.gstride = std::max(ws.gstride, 2LL * sd.nca * sd.nav);
+    gstride = 0;
+    for (const SysDev& sd : sys) gstride = std::max(gstride, sd.gstride);
     if (sys.empty()) return 0;
     const int k = (int)sys.size();
     CK(cudaMemcpy(ctx->d_bsys, sys.data(), sizeof(SysDev) * k, cudaMemcpyHostToDevice));
@@ -2173,8 +2030,8 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
 
 // n_steps steps of one width's walk set: launches of `spl` steps (the reporting interval), each
 // one sort + one walk, replayed from a CUDA graph when the lead context asks for it
-static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int64_t n_steps, int wpb, int64_t spl,
-                     int accumulate, bool graph) {
+static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstride, int64_t n_steps, int wpb,
+                     int64_t spl, int accumulate, bool graph) {
     WalkLaunch L;
     L.wpb = wpb;
     L.accumulate = accumulate;
@@ -2182,26 +2039,25 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int64_t n_
     const int64_t nfull = n_steps / spl, rem = n_steps % spl;
     if (graph && nfull > 0) {
         if (int r = walk_sort_prepare(ctx, ws.nslots)) return r;
-        if (int r = walk_attr_prepare(ctx, W, wpb, cap)) return r;
-        if (int r = walk_gscr_prepare(ctx, ws.nslots * ws.gstride)) return r;
+        if (int r = walk_attr_prepare(ctx, W, cta_smem_bytes(std::min(wpb, MRQ_MAXNW), cap, gstride))) return r;
         mrq_ctx::GraphKey key;
         key.sys = ws.systems;
         key.wptr = ws.walkers;
         key.off = ws.offsets;
         key.keys = ctx->d_sort_keys;
-        key.gscr = ctx->d_gscr;
         key.nslots = ws.nslots;
         key.k = ws.nsys;
         key.wpb = wpb;
         key.spl = (int)spl;
         key.cap = cap;
+        key.gstride = gstride;
         cudaGraphExec_t& ex = ctx->gexec[W - 1];
         if (!ex || !(ctx->gkey[W - 1] == key)) {
             if (ex) CK(cudaGraphExecDestroy(ex));
             ex = nullptr;
             CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             L.captured = true;
-            const int r = launch_walk(ctx, W, ws, (int)spl, cap, L);
+            const int r = launch_walk(ctx, W, ws, (int)spl, cap, gstride, L);
             cudaGraph_t g = nullptr;
             const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
             if (r || e != cudaSuccess) {
@@ -2221,10 +2077,10 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int64_t n_
         L.captured = false;
     } else {
         for (int64_t i = 0; i < nfull; i++)
-            if (int r = launch_walk(ctx, W, ws, (int)spl, cap, L)) return r;
+            if (int r = launch_walk(ctx, W, ws, (int)spl, cap, gstride, L)) return r;
     }
     if (rem > 0)
-        if (int r = launch_walk(ctx, W, ws, (int)rem, cap, L)) return r;
+        if (int r = launch_walk(ctx, W, ws, (int)rem, cap, gstride, L)) return r;
     return 0;
 }
 
@@ -2243,7 +2099,8 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
     for (int W = 1; W <= 2; W++) {
         WalkSet ws;
         int cap = 1;
-        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap)) return r;
+        int gstride = 0;
+        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap, gstride)) return r;
         if (ws.nsys == 0) continue;
         const size_t q = (size_t)ctx->launches * 2;
         while (ctx->evs.size() < q + 2) {
@@ -2252,21 +2109,27 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
             ctx->evs.push_back(ev);
         }
         CK(cudaEventRecord(ctx->evs[q], ctx->stream));
-        if (int r = batch_run(ctx, W, ws, cap, n_steps, lead->wpb, lead->spl, 1, lead->use_graph != 0)) return r;
+        int nw = lead->wpb;
+        if (nw <= 0)
+            for (int i = 0; i < n; i++)
+                if (ctxs[i]->W == W) nw = std::max(nw, auto_warps(ctxs[i]->hsys));
+        if (int r = batch_run(ctx, W, ws, cap, gstride, n_steps, nw, lead->spl, 1, lead->use_graph != 0))
+            return r;
         CK(cudaEventRecord(ctx->evs[q + 1], ctx->stream));
         ctx->launches++;
-        CK(cudaStreamSynchronize(ctx->stream));   // the tables are reused by the next width
+        if (int r_ = sync_stream(ctx)) return r_;   // the tables are reused by the next width
     }
     for (int i = 0; i < n; i++) ctxs[i]->total_steps += n_steps * ctxs[i]->nwalk;
     return 0;
 }
 
-int mrq_set_launch(mrq_ctx* ctx, int warps_per_block, int steps_per_launch, int use_graph) {
+int mrq_set_launch(mrq_ctx* ctx, int warps_per_walker, int steps_per_launch, int use_graph) {
     if (!ctx) return MRQ_INVALID_ARG;
-    if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4)
-        return fail(ctx, MRQ_INVALID_ARG, "warps_per_block must be 1, 2 or 4");
+    if (warps_per_walker != 0 && warps_per_walker != 1 && warps_per_walker != 2 && warps_per_walker != 4 &&
+        warps_per_walker != 8)
+        return fail(ctx, MRQ_INVALID_ARG, "warps_per_walker must be 0 (automatic), 1, 2, 4 or 8");
     if (steps_per_launch < 0) return fail(ctx, MRQ_INVALID_ARG, "steps_per_launch must be >= 0");
-    ctx->wpb = warps_per_block;
+    ctx->wpb = warps_per_walker;
     ctx->spl = steps_per_launch;
     ctx->use_graph = use_graph != 0;
     return 0;
@@ -2301,7 +2164,7 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
                                ctx->stream));
         return 0;
     };
-    const int wpbs[3] = {1, 2, 4};
+    const int wpbs[3] = {2, 4, 8};
     std::vector<int64_t> spls;
     for (int64_t v : {(int64_t)1, (int64_t)4, (int64_t)16})
         if (v <= trial_steps) spls.push_back(v);
@@ -2309,7 +2172,7 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
     double best = 1e300;
     int reps = 3;
     for (int pass = -1; pass < (int)(3 * spls.size()); pass++) {
-        const int wpb = pass < 0 ? 4 : wpbs[pass / (int)spls.size()];
+        const int wpb = pass < 0 ? 8 : wpbs[pass / (int)spls.size()];
         const int64_t spl = pass < 0 ? 1 : spls[pass % spls.size()];
         double ms_best = 1e300;
         for (int rep = 0; rep < (pass < 0 ? 1 : reps); rep++) {
@@ -2318,10 +2181,11 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
             for (int W = 1; W <= 2; W++) {
                 WalkSet ws;
                 int cap = 1;
-                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap)) return r;
+                int gstride = 0;
+                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap, gstride)) return r;
                 if (ws.nsys == 0) continue;
-                if (int r = batch_run(ctx, W, ws, cap, trial_steps, wpb, spl, 0, false)) return r;
-                CK(cudaStreamSynchronize(ctx->stream));
+                if (int r = batch_run(ctx, W, ws, cap, gstride, trial_steps, wpb, spl, 0, false)) return r;
+                if (int r_ = sync_stream(ctx)) return r_;
             }
             CK(cudaEventRecord(ctx->ev1, ctx->stream));
             CK(cudaEventSynchronize(ctx->ev1));
@@ -2332,19 +2196,19 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
         }
         if (pass < 0) continue;            // warm-up
         if (res.n_tried < MRQ_TUNE_MAX) {
-            res.tried_warps_per_block[res.n_tried] = wpb;
+            res.tried_warps_per_walker[res.n_tried] = wpb;
             res.tried_steps_per_launch[res.n_tried] = (int)spl;
             res.tried_ms[res.n_tried] = ms_best;
             res.n_tried++;
         }
         if (ms_best < best) {
             best = ms_best;
-            res.warps_per_block = wpb;
+            res.warps_per_walker = wpb;
             res.steps_per_launch = (int)spl;
         }
     }
     for (int i = 0; i < n; i++) {
-        ctxs[i]->wpb = res.warps_per_block;
+        ctxs[i]->wpb = res.warps_per_walker;
         ctxs[i]->spl = res.steps_per_launch;
     }
     if (out) *out = res;
@@ -2394,6 +2258,7 @@ int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW
     if (!ctx) return MRQ_INVALID_ARG;
     if (!ctx->d_accN) return fail(ctx, MRQ_NOT_LOADED, "no accumulators");
     CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
     const long long L = ctx->nlab * ctx->G;
     if (accN) CK(cudaMemcpyAsync(accN, ctx->d_accN, sizeof(double) * L, cudaMemcpyDeviceToHost, ctx->stream));
     if (accU) CK(cudaMemcpyAsync(accU, ctx->d_accU, sizeof(double) * L, cudaMemcpyDeviceToHost, ctx->stream));
@@ -2401,38 +2266,96 @@ int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW
     if (accE) CK(cudaMemcpyAsync(accE, ctx->d_accE, sizeof(double) * ctx->G, cudaMemcpyDeviceToHost, ctx->stream));
     if (type_steps)
         CK(cudaMemcpyAsync(type_steps, ctx->d_types, sizeof(int64_t) * MRQ_NTYPES, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     return 0;
 }
-
-#ifdef MRQ_PHASE_TIMING
-int mrq_phase_times(unsigned long long* out8) {
-    cudaDeviceSynchronize();
-    cudaMemcpyFromSymbol(out8, g_phase, sizeof(unsigned long long) * 8);
-    unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaMemcpyToSymbol(g_phase, z, sizeof z);
-    return 0;
-}
-#endif
 
 int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB) {
     if (!ctx) return MRQ_INVALID_ARG;
     if (!ctx->d_accA) return fail(ctx, MRQ_NOT_LOADED, "no accumulators");
     CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
     const size_t bytes = sizeof(double) * ctx->nlab * ctx->G;
     if (accA) CK(cudaMemcpyAsync(accA, ctx->d_accA, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     if (accB) CK(cudaMemcpyAsync(accB, ctx->d_accB, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     return 0;
 }
+
+int mrq_debug_race_clocks(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, float* screen,
+                          double* exact) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (n <= 0 || !k53 || !rate || !screen || !exact) return fail(ctx, MRQ_INVALID_ARG, "bad arguments");
+    for (int64_t i = 0; i < n; i++)
+        if (k53[i] >= (1ull << 53)) return fail(ctx, MRQ_INVALID_ARG, "k53[%lld] has more than 53 bits", (long long)i);
+    CK(cudaSetDevice(ctx->device));
+    unsigned long long* d_k = nullptr;
+    double *d_r = nullptr, *d_e = nullptr;
+    float* d_s = nullptr;
+    CK(cudaMalloc(&d_k, sizeof(unsigned long long) * n));
+    CK(cudaMalloc(&d_r, sizeof(double) * n));
+    CK(cudaMalloc(&d_e, sizeof(double) * n));
+    CK(cudaMalloc(&d_s, sizeof(float) * n));
+    CK(cudaMemcpyAsync(d_k, k53, sizeof(unsigned long long) * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(d_r, rate, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    k_race_clocks<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(d_k, d_r, n, d_s, d_e);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(screen, d_s, sizeof(float) * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(exact, d_e, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
+    cudaFree(d_k);
+    cudaFree(d_r);
+    cudaFree(d_e);
+    cudaFree(d_s);
+    return 0;
+}
+
+int mrq_set_l2_window(mrq_ctx* ctx, double fraction) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(ctx, MRQ_INVALID_ARG, "fraction must be in [0, 1]");
+    ctx->l2_fraction = fraction;
+    return 0;
+}
+
+int mrq_set_deadline(mrq_ctx* ctx, double seconds) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (!(seconds >= 0.0)) return fail(ctx, MRQ_INVALID_ARG, "deadline must be >= 0 seconds");
+    ctx->deadline_s = seconds;
+    return 0;
+}
+
+int mrq_debug_set_limits(mrq_ctx* ctx, int max_probe, int cand_cap) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    if (max_probe < 0 || max_probe > 64 || cand_cap < 0) return fail(ctx, MRQ_INVALID_ARG, "need 0 <= max_probe <= 64, cand_cap >= 0");
+    ctx->probe_limit = max_probe;
+    ctx->cap_limit = cand_cap;
+    if (ctx->ham) {
+        CK(cudaSetDevice(ctx->device));
+        if (int r = push_sys(ctx)) return r;
+    }
+    return 0;
+}
+
+#ifdef MRQ_PHASE_TIMING
+// timing builds only: the walk's per-phase SM cycles since the last call (ten counters)
+int mrq_phase_times(unsigned long long* out10) {
+    cudaDeviceSynchronize();
+    cudaMemcpyFromSymbol(out10, g_phase, sizeof(unsigned long long) * 10);
+    unsigned long long z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    cudaMemcpyToSymbol(g_phase, z, sizeof z);
+    return 0;
+}
+#endif
 
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
     if (!ctx) return MRQ_INVALID_ARG;
     if (!ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
     CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
     std::vector<Walker> w(ctx->nwalk);
     CK(cudaMemcpyAsync(w.data(), ctx->d_walk, sizeof(Walker) * ctx->nwalk, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (int r_ = sync_stream(ctx)) return r_;
     const int W = ctx->W;
     for (long long i = 0; i < ctx->nwalk; i++) {
         if (dets)

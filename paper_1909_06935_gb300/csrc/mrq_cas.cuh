@@ -13,15 +13,6 @@
 // in lockstep; the k = n term needs no lookup.  Every neighbour and every candidate of the plain
 // enumeration is visited exactly once, so the sums are the same as in local_eval.
 
-#ifdef MRQ_PHASE_TIMING
-__device__ unsigned long long g_phase[8];
-#define PHASE_T0() long long _pt0 = clock64()
-#define PHASE_ADD(k) do { long long _pt1 = clock64(); if ((threadIdx.x & 31) == 0) atomicAdd(&g_phase[k], (unsigned long long)(_pt1 - _pt0)); _pt0 = _pt1; } while (0)
-#else
-#define PHASE_T0()
-#define PHASE_ADD(k)
-#endif
-
 __device__ __forceinline__ int nsub(int cnt, int size) {
     return size == 0 ? 1 : (size == 1 ? cnt : cnt * (cnt - 1) / 2);
 }
@@ -32,12 +23,25 @@ __device__ __forceinline__ int nth_bit64(unsigned long long m, int k) {
     return __ffsll(m) - 1;
 }
 
+// pair index -> (i < j), lexicographic among k <= 128 items, from the co-lexicographic table
+// (colex[q] = i | j << 8 for q = j(j-1)/2 + i): the same map as lex_decode without a square root
+__device__ __forceinline__ void lex_decode_tab(const unsigned short* __restrict__ colex, int op, int k, int& i, int& j) {
+    const unsigned e = __ldg(colex + (k * (k - 1) / 2 - 1 - op));
+    i = k - 1 - (int)(e >> 8);
+    j = k - 1 - (int)(e & 255u);
+}
+
+// floor(x / d) for x * d < 2^32 from m = magic32(d) (m = 0 stands for d = 1)
+__device__ __forceinline__ unsigned magic32(unsigned d) { return d > 1u ? 0xFFFFFFFFu / d + 1u : 0u; }
+__device__ __forceinline__ unsigned div_m(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
+
 // the idx-th subset of `size` (0..2) set bits of m (cnt = popcount of m), lexicographic
-__device__ __forceinline__ unsigned long long subset_bits(unsigned long long m, int cnt, int size, int idx) {
+__device__ __forceinline__ unsigned long long subset_bits(const unsigned short* __restrict__ colex, unsigned long long m,
+                                                          int cnt, int size, int idx) {
     if (size == 0) return 0ull;
     if (size == 1) return 1ull << nth_bit64(m, idx);
     int i, j;
-    lex_decode(idx, cnt, i, j);
+    lex_decode_tab(colex, idx, cnt, i, j);
     return (1ull << nth_bit64(m, i)) | (1ull << nth_bit64(m, j));
 }
 
@@ -62,18 +66,20 @@ __device__ __forceinline__ int shape_count(int m, int cnt, int nal) {
     return nal == 1 ? m * m : m * (m - 1) / 2;
 }
 
-// idx-th choice of that shape as sorted spin orbitals; orbitals of the space start at `off`
-__device__ __forceinline__ void shape_decode(const SysDev& S, int m, int cnt, int nal, int off, int idx, int* out) {
+// idx-th choice of that shape as sorted spin orbitals; orbitals of the space start at `off`;
+// mag = ceil(2^64 / m) (0 when m = 1) for the alpha-beta division
+__device__ __forceinline__ void shape_decode(const SysDev& S, int m, int cnt, int nal, int off, int idx, int* out,
+                                             unsigned long long mag) {
     if (cnt == 1) {
         out[0] = (nal ? 0 : S.n) + off + idx;
     } else if (cnt == 2) {
         if (nal == 1) {
-            int i = idx / m, j = idx - i * m;
+            const int i = mag ? (int)__umul64hi((unsigned long long)idx, mag) : idx, j = idx - i * m;
             out[0] = off + i;
             out[1] = S.n + off + j;
         } else {
             int i, j;
-            lex_decode(idx, m, i, j);
+            lex_decode_tab(S.colex, idx, m, i, j);
             const int base = (nal == 2 ? 0 : S.n) + off;
             out[0] = base + i;
             out[1] = base + j;
@@ -229,8 +235,8 @@ __device__ __forceinline__ void dbl_entry(const SysDev& S, const unsigned long l
 __device__ __forceinline__ void lane_offsets(const SysDev& S, int c, int v, int xc0, int xc1, int yv0, int yv1,
                                              unsigned& off_d, unsigned& off_x, int& par) {
     const unsigned sv = (unsigned)S.nav, sq = sv * sv, sp = sq * (unsigned)S.nca;
-    const unsigned p0 = (unsigned)(xc0 % S.n), p1 = (unsigned)(xc1 % S.n);
-    const unsigned v0 = (unsigned)(yv0 % S.n - S.nc), v1 = (unsigned)(yv1 % S.n - S.nc);
+    const unsigned p0 = (unsigned)(xc0 - (xc0 >= S.n ? S.n : 0)), p1 = (unsigned)(xc1 - (xc1 >= S.n ? S.n : 0));
+    const unsigned v0 = (unsigned)(yv0 - (yv0 >= S.n ? S.n : 0) - S.nc), v1 = (unsigned)(yv1 - (yv1 >= S.n ? S.n : 0) - S.nc);
     const unsigned core = c == 2 ? p0 * sp + p1 * sq : (c == 1 ? p0 * sq : 0u);
     off_d = core + (v == 2 ? v0 * sv + v1 : (v == 1 ? v0 : 0u));
     off_x = core + (v == 2 ? v1 * sv + v0 : (v == 1 ? v0 * sv : 0u));
@@ -283,35 +289,11 @@ __device__ __forceinline__ double cand_sum(const SysDev& S, const unsigned long 
 
 // The walker's single-excitation operator, for every hole y (core or active) and electron x (active
 // or virtual) of one spin s:  G^s_yx(n) = hc_yx + sum_{j in act occ(n)} (yx|jj) - sum_{j in act occ_s(n)} (yj|jx)
-// (n a CAS determinant: full core, empty virtuals).  Slater-Condon gives, for a neighbour
-// m = n - R + A and its single x -> y,  <k|H|m> = sign (G^s_yx(n) + sum_{j in A} f(j) - sum_{j in R} f(j)),
-// f(j) = (yx|jj) - d_{s_j s} (yj|jx): the same sum as single_elem over occ(m), with <= 4 corrections in
-// place of one term per occupied orbital.  g: 2 x nca x nav doubles, [s][y][x - nc]; the
-// active-active block is not needed (no single of a FOIS neighbour stays in the active space).
-template <class C>
-__device__ void walker_single_ops(const SysDev& S, unsigned long long AOn, double* __restrict__ g, int lane, C& ctr) {
-    const int nc = S.nc, na = S.na, n = S.n, nca = S.nca, nav = S.nav, blk = nca * nav;
-    for (int t = lane; t < 2 * blk; t += 32) {
-        const int sg = t >= blk, rem = t - sg * blk;
-        const int y = rem / nav, xo = rem - y * nav, x = nc + xo;
-        if (y >= nc && xo < na) continue;
-        ctr.g();
-        double v = __ldg(S.hc + y * n + x);
-        unsigned long long bits = AOn;
-        while (bits) {
-            const int b = __ffsll(bits) - 1;
-            bits &= bits - 1;
-            const int j = nc + (b & 31);
-            v += eri_g(S, y, x, j, j);
-            ctr.g();
-            if ((b >= 32) == (sg == 1)) {
-                v -= eri_g(S, y, j, j, x);
-                ctr.g();
-            }
-        }
-        g[t] = v;
-    }
-}
+// (n a CAS determinant: full core, empty virtuals), tabulated per walker step by the walk block
+// (2 x nca x nav doubles, [s][y][x - nc]; the active-active block is not needed).  Slater-Condon
+// gives, for a neighbour m = n - R + A and its single x -> y,  <k|H|m> = sign (G^s_yx(n) +
+// sum_{j in A} f(j) - sum_{j in R} f(j)), f(j) = (yx|jj) - d_{s_j s} (yj|jx): the same sum as
+// single_elem over occ(m), with <= 4 corrections in place of one term per occupied orbital.
 
 // f(j) of one orbital j (spin orbital) for the single x -> y of spin sx (spatial px, py)
 __device__ __forceinline__ double single_corr(const SysDev& S, int sx, int px, int py, int j) {
@@ -336,7 +318,7 @@ __device__ __forceinline__ double sgl_elem_code(const SysDev& S, const double* g
     v += single_corr(S, sx, px, py, ad0) - single_corr(S, sx, px, py, rm0);
     if (r == 2) v += single_corr(S, sx, px, py, ad1) - single_corr(S, sx, px, py, rm1);
     ctr.g(1 + 4 * r);
-    return sgn_single<W>(m[sx], px, py) * v;
+    return neg_if(v, popc_between<W>(m[sx], min(px, py), max(px, py)));
 }
 
 // the cnt (1 or 2) items made of k1 "first" items (f0, f1) and then (s0, s1), sorted when cnt = 2
@@ -358,8 +340,8 @@ __device__ __forceinline__ void group_neighbour(const SysDev& S, const unsigned 
                                                 int& yv0, int& yv1, int& rm0, int& rm1, int& ad0, int& ad1,
                                                 unsigned long long (&m)[2][W]) {
     int t[2] = {0, 0}, u[2] = {0, 0};
-    shape_decode(S, nc, c, sc, 0, ic, t);
-    shape_decode(S, nv, v, sv, voff, iv, u);
+    shape_decode(S, nc, c, sc, 0, ic, t, S.mag_c);
+    shape_decode(S, nv, v, sv, voff, iv, u, S.mag_v);
     xc0 = t[0];
     xc1 = t[1];
     yv0 = u[0];
@@ -380,259 +362,4 @@ __device__ __forceinline__ void group_neighbour(const SysDev& S, const unsigned 
         flip<W>(m[s1], rm1 - s1 * S.n);
         flip<W>(m[s2], ad1 - s2 * S.n);
     }
-}
-
-template <int W, int MODE, class C>
-__device__ LocalOut local_eval_cas(const SysDev& S, WarpSh& sh, double* cphi, unsigned* ccode,
-                                   const unsigned long long (&n)[2][W], double psin, unsigned step, unsigned wid,
-                                   int lane, unsigned long long (&best)[2][W], double& best_psi, unsigned& best_exc,
-                                   mrq_neighbour* nbout, long long max_nb, C& ctr, double* gops) {
-    build_lists<W>(S, n, sh, 0, 0, lane);          // occupied lists for the diagonal sums
-    const int nc = S.nc, nv = S.nv, voff = S.nc + S.na;
-    const double c0 = __ldg(S.c);
-    const double inv_psin = psin != 0.0 ? 1.0 / psin : 0.0;
-    const double phin = psin / c0;
-    const unsigned ao0 = active_bits<W>(S, n[0]), ao1 = active_bits<W>(S, n[1]);
-    const unsigned amask = (S.na >= 32) ? 0xFFFFFFFFu : ((1u << S.na) - 1u);
-    const unsigned long long AOn = (unsigned long long)ao0 | ((unsigned long long)ao1 << 32);
-    const unsigned long long AEn =
-        (unsigned long long)(~ao0 & amask) | ((unsigned long long)(~ao1 & amask) << 32);
-    const unsigned long long keyn = hash_key(S, ao0, ao1);
-    const int cntO = __popcll(AOn), cntE = __popcll(AEn);
-    const unsigned lt = (1u << lane) - 1u;
-    LaneAcc<W> acc;
-    lane_acc_init<W>(acc, n);
-    int nbase = 0;     // running neighbour index (debug records)
-    PHASE_T0();
-    if (gops != nullptr) {
-        walker_single_ops(S, AOn, gops, lane, ctr);
-        __syncwarp();
-    }
-
-    // (a) neighbours inside the CAS: active singles and doubles of n
-    for (int r = 1; r <= 2; r++) {
-        const int nY = nsub(cntE, r), tot = nsub(cntO, r) * nY;
-        for (int base = 0; base < tot; base += 32) {
-            const int t = base + lane;
-            bool valid = t < tot;
-            unsigned long long Xb = 0, Yb = 0;
-            if (valid) {
-                const int ix = t / nY;
-                Xb = subset_bits(AOn, cntO, r, ix);
-                Yb = subset_bits(AEn, cntE, r, t - ix * nY);
-                valid = __popcll(Xb & 0xFFFFFFFFull) == __popcll(Yb & 0xFFFFFFFFull);
-            }
-            const unsigned vm = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
-                int rem[2], add[2];
-                act_list(S, Xb, rem);
-                act_list(S, Yb, add);
-                unsigned long long m[2][W];
-#pragma unroll
-                for (int sg = 0; sg < 2; sg++)
-#pragma unroll
-                    for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
-                apply_exc<W>(m, S, rem, add, r);
-                const double hnm = r == 1 ? single_elem<W>(S, n, rem[0], add[0], ctr)
-                                          : double_elem<W>(S, n, rem[0], rem[1], add[0], add[1], ctr);
-                const unsigned long long km = (AOn & ~Xb) | Yb;
-                ctr.cand();
-                const double om = hash_lookup(S, hash_key(S, (unsigned)km, (unsigned)(km >> 32)), ctr);
-                const unsigned exc = r == 1 ? ((unsigned)rem[0] | ((unsigned)rem[0] << 8) | ((unsigned)add[0] << 16) |
-                                               ((unsigned)add[0] << 24))
-                                            : ((unsigned)rem[0] | ((unsigned)rem[1] << 8) | ((unsigned)add[0] << 16) |
-                                               ((unsigned)add[1] << 24));
-                const long long ri = nbase + __popc(vm & lt);
-                lane_post<W, MODE>(S, acc, m, hnm, 0.0, false, om, c0 * om, inv_psin, exc, step, wid,
-                                   (MODE == MODE_DEBUG && nbout != nullptr && ri < max_nb) ? nbout + ri : nullptr);
-            }
-            nbase += __popc(vm);
-        }
-    }
-
-    PHASE_ADD(0);
-    // (b) neighbours in the FOIS, group by group
-    for (int ka = 0; ka <= 2; ka++) {
-        for (int kb = 0; kb <= 2; kb++) {
-            if (ka == 2 && kb == 2) continue;                   // no room left for core / virtual moves
-            const int nXa = nsub(cntO, ka), nYa = nsub(cntE, kb);
-            for (int xa = 0; xa < nXa; xa++) {
-                const unsigned long long Xb = subset_bits(AOn, cntO, ka, xa);
-                for (int ya = 0; ya < nYa; ya++) {
-                    const unsigned long long Yb = subset_bits(AEn, cntE, kb, ya);
-                    // alpha balance: alpha(X_c) - alpha(Y_v) = alpha(Y_a) - alpha(X_a)
-                    const int d = __popcll(Yb & 0xFFFFFFFFull) - __popcll(Xb & 0xFFFFFFFFull);
-                    const unsigned long long AOm = (AOn & ~Xb) | Yb, AEm = (AEn & ~Yb) | Xb;
-                    const int cO = __popcll(AOm), cE = __popcll(AEm);
-                    // the group's active electrons removed (xa0, xa1) and holes filled (ya0, ya1)
-                    const int xa0 = Xb ? act_so(S, __ffsll(Xb) - 1) : 0;
-                    const int xa1 = (ka == 2) ? act_so(S, 63 - __clzll(Xb)) : 0;
-                    const int ya0 = Yb ? act_so(S, __ffsll(Yb) - 1) : 0;
-                    const int ya1 = (kb == 2) ? act_so(S, 63 - __clzll(Yb)) : 0;
-                    const int rmin = max(1, max(ka, kb));
-                    for (int r = rmin; r <= 2; r++) {
-                        const int c = r - ka, v = r - kb;
-                        if (c == 0 && v == 0) continue;
-                        for (int sc = 0; sc <= c; sc++) {
-                            const int sv = sc - d;
-                            if (sv < 0 || sv > v) continue;
-                            const int ncc = shape_count(nc, c, sc), nvc = shape_count(nv, v, sv);
-                            const int ni = ncc * nvc;
-                            if (ni == 0) continue;
-                            PHASE_ADD(1);
-                            // reference lane (the group's first neighbour) for the candidates' signs
-                            int rxc0, rxc1, ryv0, ryv1, rrm0, rrm1, rad0, rad1;
-                            unsigned long long mref[2][W];
-                            group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, 0, 0, ka, xa0, xa1, kb, ya0, ya1, r,
-                                               rxc0, rxc1, ryv0, ryv1, rrm0, rrm1, rad0, rad1, mref);
-                            const int par_ref = (c >= 1 ? rxc0 % S.n : 0) + (c == 2 ? rxc1 % S.n : 0);
-                            // ---- the group's candidate list (k = n excluded): singles [0, n1) as codes,
-                            // doubles [n1, count) as (signed weight, table base)
-                            int count = 0, n1 = 0;
-                            for (int rr = 1; rr <= 2; rr++) {
-                                if (rr == 2) n1 = count;
-                                if (rr == 1 && (c > 1 || v > 1)) continue;
-                                const int ne = rr - v, nf = rr - c;
-                                if (ne < 0 || nf < 0) continue;
-                                const int nA = nsub(cE, nf), tot = nsub(cO, ne) * nA;
-                                for (int base = 0; base < tot; base += 32) {
-                                    const int t = base + lane;
-                                    bool valid = t < tot;
-                                    unsigned long long Rb = 0, Ab = 0;
-                                    double phi = 0.0;
-                                    if (valid) {
-                                        const int iR = t / nA;
-                                        Rb = subset_bits(AOm, cO, ne, iR);
-                                        Ab = subset_bits(AEm, cE, nf, t - iR * nA);
-                                        valid = sv + __popcll(Rb & 0xFFFFFFFFull) == sc + __popcll(Ab & 0xFFFFFFFFull);
-                                    }
-                                    if (valid) {
-                                        const unsigned long long kact = (AOm & ~Rb) | Ab;
-                                        const unsigned long long key = hash_key(S, (unsigned)kact, (unsigned)(kact >> 32));
-                                        ctr.cand();
-                                        if (key == keyn) valid = false;
-                                        else {
-                                            phi = hash_lookup(S, key, ctr);
-                                            valid = phi != 0.0;
-                                        }
-                                    }
-                                    const unsigned vm = __ballot_sync(0xffffffffu, valid);
-                                    if (valid) {
-                                        const int pos = count + __popc(vm & lt);
-                                        if (pos < S.cand_cap) {
-                                            if (rr == 1) {
-                                                cphi[pos] = phi;
-                                                ccode[pos] = pack_cand(Rb, Ab, rr);
-                                            } else {
-                                                double w;
-                                                unsigned bp;
-                                                dbl_entry<W>(S, mref, c, v, rxc0, rxc1, ryv0, ryv1, par_ref, Rb, Ab,
-                                                             phi, w, bp);
-                                                cphi[pos] = w;
-                                                ccode[pos] = bp;
-                                            }
-                                        }
-                                    }
-                                    count += __popc(vm);
-                                }
-                            }
-                            if (count > S.cand_cap) {
-                                if (lane == 0) atomicOr(S.err, MRQ_ERR_CAP);
-                                count = S.cand_cap;
-                                n1 = min(n1, count);
-                            }
-                            __syncwarp();
-                            PHASE_ADD(2);
-                            // ---- the group's neighbours: wide groups one lane per neighbour; narrow
-                            // groups one neighbour at a time with the lanes over its candidates
-                            // lane per neighbour (wide: lanes differ in a core / virtual orbital, so their
-                            // integral gathers are adjacent), or for small groups one neighbour at a time with
-                            // the lanes over its candidates (narrow), 32 neighbours per chunk
-                            const bool wide = ni >= 16;
-                            for (int rd = 0; rd < (ni + 31) / 32; rd++) {
-                                double o_narrow = 0.0;
-                                if (!wide) {
-                                    const int qend = min(ni, rd * 32 + 32);
-                                    for (int q = rd * 32; q < qend; q++) {
-                                        int xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1;
-                                        unsigned long long m[2][W];
-                                        const int ic = q / nvc;
-                                        group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, ic, q - ic * nvc, ka, xa0,
-                                                           xa1, kb, ya0, ya1, r, xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1, m);
-                                        double part = 0.0;
-                                        for (int e = lane; e < n1; e += 32)
-                                            part = fma(cphi[e],
-                                                       sgl_elem_code<W>(S, gops, m, ccode[e], v, yv0, c, xc0, r, rm0,
-                                                                        rm1, ad0, ad1, ctr),
-                                                       part);
-                                        unsigned offd, offx;
-                                        int par;
-                                        lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
-                                        part += neg_if(tab_sum(S, cphi, ccode, n1 + lane, count, 32, offd, offx, ctr), par);
-                                        const double o = warp_sum(part);
-                                        if (lane == q - rd * 32) o_narrow = o;
-                                    }
-                                }
-                                const int q = rd * 32 + lane;
-                                if (q < ni) {
-                                    int xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1;
-                                    unsigned long long m[2][W];
-                                    const int ic = q / nvc;
-                                    group_neighbour<W>(S, n, nc, nv, voff, c, sc, v, sv, ic, q - ic * nvc, ka, xa0, xa1,
-                                                       kb, ya0, ya1, r, xc0, xc1, yv0, yv1, rm0, rm1, ad0, ad1, m);
-                                    const double hnm = r == 1 ? single_elem<W>(S, n, rm0, ad0, ctr)
-                                                              : double_elem<W>(S, n, rm0, rm1, ad0, ad1, ctr);
-                                    double om = hnm * phin;        // the k = n term
-                                    if (wide) {
-                                        double part = 0.0;
-                                        PHASE_ADD(3);
-                                        for (int e = 0; e < n1; e++)
-                                            part = fma(cphi[e],
-                                                       sgl_elem_code<W>(S, gops, m, ccode[e], v, yv0, c, xc0, r, rm0,
-                                                                        rm1, ad0, ad1, ctr),
-                                                       part);
-                                        PHASE_ADD(7);
-                                        unsigned offd, offx;
-                                        int par;
-                                        lane_offsets(S, c, v, xc0, xc1, yv0, yv1, offd, offx, par);
-                                        part += neg_if(tab_sum(S, cphi, ccode, n1, count, 1, offd, offx, ctr), par);
-                                        om += part;
-                                    } else {
-                                        om += o_narrow;
-                                    }
-                                    ctr.term(count + 1);
-                                    // label of m: holes xc, particles yv
-                                    const int h0 = xc0 >= S.n ? nc + (xc0 - S.n) : xc0;
-                                    const int h1 = xc1 >= S.n ? nc + (xc1 - S.n) : xc1;
-                                    const int p0 = yv0 >= S.n ? nv + (yv0 - S.n - voff) : yv0 - voff;
-                                    const int p1 = yv1 >= S.n ? nv + (yv1 - S.n - voff) : yv1 - voff;
-                                    const long long lm =
-                                        set_rank(c, h0, h1, 2 * nc) * S.nPs + set_rank(v, p0, p1, 2 * nv);
-                                    ctr.g();
-                                    const double psim = __ldg(S.c + lm) * om;
-                                    const unsigned exc =
-                                        r == 1 ? ((unsigned)rm0 | ((unsigned)rm0 << 8) | ((unsigned)ad0 << 16) |
-                                                  ((unsigned)ad0 << 24))
-                                               : ((unsigned)rm0 | ((unsigned)rm1 << 8) | ((unsigned)ad0 << 16) |
-                                                  ((unsigned)ad1 << 24));
-                                    const long long ri = nbase + q;
-                                    lane_post<W, MODE>(S, acc, m, hnm, 0.0, false, om, psim, inv_psin, exc, step, wid,
-                                                       (MODE == MODE_DEBUG && nbout != nullptr && ri < max_nb)
-                                                           ? nbout + ri
-                                                           : nullptr);
-                                }
-                            }
-                            nbase += ni;
-                            __syncwarp();
-                            if (wide) PHASE_ADD(3); else PHASE_ADD(4);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    PHASE_ADD(1);
-    LocalOut lo = finish_local<W, MODE>(S, sh, n, 0, lane, acc, nbase, best, best_psi, best_exc);
-    PHASE_ADD(5);
-    return lo;
 }

@@ -62,6 +62,17 @@ struct SysDev {
     long long burn_in;
     unsigned long long seed;
     int* err;
+    // work-unit plan of a CAS walker's step (the same for every CAS determinant of the system:
+    // they all hold the same numbers of active alpha and beta electrons)
+    long long cas_nb_total;  // neighbours of a CAS determinant
+    int cas_nb;              // of them inside the CAS
+    int cas_units;           // units covering those (MRQ_CAS_CH each)
+    int unit_off[9];         // first unit of pair class k = 3 ka + kb (k < 8); unit_off[8] = all units
+    int nch[8];              // chunks per (X_a, Y_a) pair of class k
+    int gstride;             // doubles of the walker's single-excitation operator, 2 nca nav
+    int pad_;
+    const unsigned short* colex;       // pair decode table: colex[j(j-1)/2 + i] = i | j << 8, i < j < 128
+    unsigned long long mag_c, mag_v;   // ceil(2^64 / n_core), ceil(2^64 / n_virt) (0 when that is <= 1)
 };
 
 // ------------------------------------------------------------------ access counters
@@ -73,6 +84,7 @@ struct NoCtr {
     __device__ __forceinline__ void pr(int = 1) {}
     __device__ __forceinline__ void cand() {}
     __device__ __forceinline__ void term(int = 1) {}
+    __device__ __forceinline__ void mark(int) {}     // phase boundary (timing builds only)
 };
 struct Ctr {
     unsigned long long gathers = 0, probes = 0, cands = 0, terms = 0;
@@ -80,6 +92,7 @@ struct Ctr {
     __device__ __forceinline__ void pr(int k = 1) { probes += k; }
     __device__ __forceinline__ void cand() { cands++; }
     __device__ __forceinline__ void term(int k = 1) { terms += k; }   // H_mk phi0(k) products summed
+    __device__ __forceinline__ void mark(int) {}
 };
 
 // ------------------------------------------------------------------ small helpers
@@ -266,7 +279,7 @@ __device__ double single_elem(const SysDev& S, const unsigned long long (&d)[2][
             if (sg == sx) { v += eri_g(S, py, j, j, px); ctr.g(); }
         }
     }
-    return sgn_single<W>(d[sx], px, py) * v;
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_between<W>(d[sx], px < py ? px : py, px < py ? py : px) & 1) << 63));
 }
 
 // <d'|H|d> for the double r1,r2 -> a1,a2 (spin orbitals, r1<r2, a1<a2, spin conserving)
@@ -315,7 +328,7 @@ __device__ double hd_single_elem(const SysDev& S, const unsigned long long (&d)[
                 if (sg == sx) { v -= eri_g(S, py, j, j, px); ctr.g(); }
             }
         }
-    return sgn_single<W>(d[sx], px, py) * v;
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_between<W>(d[sx], px < py ? px : py, px < py ? py : px) & 1) << 63));
 }
 
 // ------------------------------------------------------------------ reach-back (Eq. 6-7)
@@ -519,10 +532,28 @@ __device__ __forceinline__ double race_clock_f64(unsigned long long k, double ra
     return -log(u) / rate;
 }
 
-// the same clock in FP32 from 1-u (exact integer, relative rounding 6e-8), for screening:
-// relative error well below 1e-4, so a candidate whose FP32 clock exceeds the best by 1e-4
-// cannot win in FP64
-__device__ __forceinline__ float race_clock_f32(unsigned long long k, float rate) {
-    const float one_minus_u = (float)(9007199254740992ull - k - 1ull) * 1.1102230246251565e-16f;
-    return -log1pf(-one_minus_u) / rate;
+// FP32 image of |x| from its bits (mantissa truncated to 23 bits, relative error < 2^-23); 0 outside
+// [2^-100, 2^100]
+__device__ __forceinline__ float abs_f32_of(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32) & 0x7FFFFFFFu;
+    const int e = (int)(hi >> 20);                       // biased exponent
+    if (e < 1023 - 100 || e > 1023 + 100) return 0.0f;
+    const unsigned f = ((unsigned)(e - 1023 + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (unsigned)((b & 0xFFFFFFFFull) >> 29);
+    return __uint_as_float(f);
+}
+
+// The race clock -ln(u)/Gamma in FP32, for screening only, from the FP32 image gf of Gamma.  For
+// u < 1/2 it is -ln(u) from u itself (u = (k+1) 2^-53 rounds to FP32 with relative error 6e-8 and
+// never underflows); for u >= 1/2 it is -log1p(-(1-u)) with 1-u = (2^53-k-1) 2^-53 (< 2^52, rounded
+// once), so the clock's relative error stays below 1e-6 for every k.  0 - which never screens a
+// candidate out, the exact FP64 clock then decides - when gf is outside [1e-30, 1e30] or the clock
+// itself falls below the normal FP32 range.
+__device__ __forceinline__ float race_screen(unsigned long long k, float gf) {
+    if (!(gf > 1e-30f && gf < 1e30f)) return 0.0f;
+    float lnu;
+    if (k < 4503599627370495ull) lnu = logf((float)(k + 1ull) * 1.1102230246251565e-16f);
+    else lnu = log1pf(-(float)(9007199254740991ull - k) * 1.1102230246251565e-16f);
+    const float t = -lnu / gf;
+    return t < 1e-37f ? 0.0f : t;
 }

@@ -67,7 +67,11 @@ int64_t footprint_of(const Request& r) {
     b += 8 * (2 * n * n + neri + npair * n * n + 2 * nca * nca * nav * nav + n + r.n_act * r.n_act);
     b += 16 * cap + 8 * nlab;
     b += 32 * G * nlab + 16 * G;        // N, U and the SC-MRCI gradient sums A, B per group
-    b += (64 + 16 * nca * nav) * r.params.n_walkers + 16 * 8192;   // walkers and their single-excitation operators
+    b += 112 * r.params.n_walkers;     // walkers with their step records
+    int64_t npad = 1;
+    while (npad < r.params.n_walkers) npad <<= 1;
+    b += 12 * npad;                     // slot ordering keys and indices
+    b += 8 * (G + 1) * ((nlab + 8191) / 8192) * 45;   // finalize partial sums
     return b;
 }
 
@@ -174,13 +178,23 @@ static int server_round(mrq_server* s) {
     const int64_t steps = s->p.steps_per_round;
     int rc = mrq_batch_advance(ctxs.data(), (int)ctxs.size(), steps);
     if (rc) snprintf(s->err, sizeof s->err, "batched advance failed: %s", mrq_last_error(ctxs[0]));
-    // 3. finalize, retire
+    // 3. finalize with the lock released (only this thread uses an active request's context, and
+    //    only this thread retires running requests), then retire under the lock
+    std::vector<mrq_result> res(act.size());
+    std::vector<int> fr(act.size(), 0);
+    if (!rc)
+        for (size_t i = 0; i < act.size(); i++) fr[i] = mrq_finalize(act[i]->ctx, &res[i]);
     std::lock_guard<std::mutex> g(s->mu);
     s->rounds++;
     std::vector<Request*> keep;
     for (Request* r : s->active) {
         if (r->state == MRQ_REQ_CANCELLED) {
             retire_locked(s, r, MRQ_REQ_CANCELLED);
+            continue;
+        }
+        const size_t i = (size_t)(std::find(act.begin(), act.end(), r) - act.begin());
+        if (i == act.size()) {          // admitted after the snapshot: nothing ran yet
+            keep.push_back(r);
             continue;
         }
         if (rc) {
@@ -190,16 +204,14 @@ static int server_round(mrq_server* s) {
         }
         r->steps_done += steps;
         s->total_walker_steps += steps * r->params.n_walkers;
-        mrq_result res{};
-        const int fr = mrq_finalize(r->ctx, &res);
-        r->result = res;
-        if (fr) {
-            r->status = fr;
+        r->result = res[i];
+        if (fr[i]) {
+            r->status = fr[i];
             retire_locked(s, r, MRQ_REQ_FAILED);
             continue;
         }
-        const bool converged = r->target_sigma > 0.0 && r->steps_done > r->params.burn_in && res.walker_steps > 0 &&
-                               res.e2_sigma <= r->target_sigma;
+        const bool converged = r->target_sigma > 0.0 && r->steps_done > r->params.burn_in &&
+                               res[i].walker_steps > 0 && res[i].e2_sigma <= r->target_sigma;
         if (converged || r->steps_done >= r->max_steps) retire_locked(s, r, MRQ_REQ_DONE);
         else keep.push_back(r);
     }

@@ -567,26 +567,35 @@ def workload(name: str) -> System:
 
 # --------------------------------------------------------------------------- batched / served workloads
 
-def batch_specs(n_sys: int = 64, seed: int = 2409, total_walkers: int = 32768):
-    """Size distribution of the batched workload: 30-120 spatial orbitals, active spaces of 6, 8 or 10
-    orbitals at half filling (references of 400, 4,900 or 63,504 determinants), 2-10 core orbitals,
-    Cholesky rank 3n; walkers per system proportional to the reference size (at least 32)."""
+def batch_specs(n_sys: int = 64, seed: int = 2409, total_walkers: int = 32768, max_act: int = 14):
+    """Size distribution of the batched workload: 30-120 spatial orbitals, active spaces of 6-14
+    orbitals at half filling, 2-10 core orbitals, Cholesky rank 3n.  Active spaces of up to 10
+    orbitals take the exact CAS-CI reference (400, 4,900 or 63,504 determinants); 12 and 14 take a
+    heat-bath selected-CI reference of 1e5 to 5e5 determinants (n_strings^2, n_strings drawn so).
+    Walkers per system are proportional to the reference size (at least 32)."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    acts = [a for a in (6, 8, 10, 12, 14) if a <= max_act]
+    prob = np.array([0.34, 0.26, 0.2, 0.12, 0.08][:len(acts)])
+    prob /= prob.sum()
     specs = []
     for k in range(n_sys):
         n = int(rng.integers(30, 121))
-        na = int(rng.choice([6, 8, 10], p=[0.5, 0.35, 0.15]))
+        na = int(rng.choice(acts, p=prob))
         nc = int(rng.integers(2, 11))
         nv = n - nc - na
-        specs.append(dict(n_core=nc, n_act=na, n_virt=nv, n_alpha=nc + na // 2, n_beta=nc + na // 2,
-                          rank=3 * n, seed=seed + 100 * (k + 1), chol_sigma=0.05))
-    ndet = np.array([len(cas_strings(s["n_act"], s["n_act"] // 2)) ** 2 for s in specs], dtype=float)
+        spec = dict(n_core=nc, n_act=na, n_virt=nv, n_alpha=nc + na // 2, n_beta=nc + na // 2,
+                    rank=3 * n, seed=seed + 100 * (k + 1), chol_sigma=0.05)
+        if na > 10:
+            spec["n_strings"] = int(round(np.sqrt(rng.uniform(1e5, 5e5))))
+        specs.append(spec)
+    ndet = np.array([s["n_strings"] ** 2 if "n_strings" in s else len(cas_strings(s["n_act"], s["n_act"] // 2)) ** 2
+                     for s in specs], dtype=float)
     walkers = np.maximum(32, np.round(total_walkers * ndet / ndet.sum())).astype(int)
     return specs, walkers.tolist()
 
 
 def _make_from_spec(spec):
-    return make_system(**spec)
+    return make_sci_system(**spec) if "n_strings" in spec else make_system(**spec)
 
 
 def make_systems(specs, processes: int = 0):
@@ -595,7 +604,7 @@ def make_systems(specs, processes: int = 0):
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(processes) as pool:
             return pool.map(_make_from_spec, specs)
-    return [make_system(**s) for s in specs]
+    return [_make_from_spec(s) for s in specs]
 
 
 def scan_systems(spec: dict, n_points: int = 10, lam_max: float = 0.1, seed: int = 7):

@@ -1,9 +1,11 @@
 """Batched form: several independent systems walked in one launch give the same result as each
-system walked alone (trajectories bit-identical; accumulators and energies to rounding, because the
-group sums are FP64 atomics whose order differs)."""
+system walked alone, bit for bit (every walker's step is evaluated by the same block code, and the
+accumulation adds each group's walkers in walker order), and the same as the oracle's walk
+(trajectories bit-identical, accumulators within 1e-10)."""
 import numpy as np
 import pytest
 
+import oracle as O
 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -45,10 +47,20 @@ def test_batch_equals_alone():
         acc_b = c.accumulators(G)
         assert np.array_equal(acc_a["type_steps"], acc_b["type_steps"])
         for key in ("N", "U", "W", "E"):
-            assert _close(acc_a[key], acc_b[key], 1e-12), (k, key)
+            assert np.array_equal(acc_a[key], acc_b[key]), (k, key)
         for key in ("e2", "e_var", "a0sq", "e2_sigma"):
-            assert _close(res_a[key], results[k][key], 1e-10), (k, key)
+            assert res_a[key] == results[k][key], (k, key)
         assert results[k]["walker_steps"] == nw * (steps - 2)
+        # and the oracle's walk of the same system, walkers and seed
+        orc = O.Oracle.from_system(systems[k])
+        acc_o = orc.sample(nw, steps, 2, seeds[k], G, trajectory=True)
+        assert np.array_equal(dets_b, acc_o["trajectory"][:, -1, :]), k
+        assert np.array_equal(acc_b["type_steps"], acc_o["type_steps"]), k
+        for key in ("N", "U", "W", "E"):
+            assert _close(acc_b[key], acc_o[key], 1e-10), (k, key)
+        fo = orc.finalize(acc_o)
+        for key in ("e2", "e_var", "a0sq", "e2_sigma"):
+            assert _close(results[k][key], fo[key], 1e-9), (k, key)
 
 
 def test_batch_advance_in_chunks_matches_single_launch():
@@ -93,10 +105,13 @@ def _run_batch(ctxs, walkers, seeds, steps, G, launch):
     return out
 
 
-@pytest.mark.parametrize("launch", [(1, 1, False), (2, 4, True), (4, 16, True), (1, 7, True), (2, 0, False)])
+@pytest.mark.parametrize("launch", [(1, 1, False), (2, 4, True), (8, 16, True), (1, 7, True), (2, 0, False),
+                                    (0, 3, True)])
 def test_launch_configuration_leaves_results_unchanged(launch):
-    """Walkers per block, steps per launch (re-ordering the slots between launches) and CUDA-graph
-    replay change the schedule only: trajectories bit-identical, accumulators to rounding."""
+    """Warps per walker, steps per launch (re-ordering the slots between launches) and CUDA-graph
+    replay change the schedule only: every walker's units form the same fixed partition whatever
+    the warps, and the accumulation adds each group's walkers in id order, so trajectories and
+    accumulators are bit-identical."""
     import paper_1909_06935_gb300 as P
     systems = _systems()
     walkers, seeds, steps, G = [128, 64, 32, 96], [21, 22, 23, 24], 40, 4
@@ -109,7 +124,7 @@ def test_launch_configuration_leaves_results_unchanged(launch):
             assert np.array_equal(ref[k][0], g[k][0]), (k, launch)
             assert np.array_equal(ref[k][1]["type_steps"], g[k][1]["type_steps"])
             for key in ("N", "U", "W", "E"):
-                assert _close(ref[k][1][key], g[k][1][key], 1e-12), (k, key)
+                assert np.array_equal(ref[k][1][key], g[k][1][key]), (k, key, launch)
     for c in ctxs:
         c.close()
 
@@ -125,7 +140,7 @@ def test_tuner_leaves_state_unchanged_and_sets_a_tried_configuration():
     before = [(c.walkers(nw)[0], c.accumulators(G)) for c, nw in zip(ctxs, walkers)]
     t = P.tune_batch(ctxs, trial_steps=16)
     assert len(t["tried"]) == 9 and all(ms > 0 for _, _, ms in t["tried"])
-    assert (t["warps_per_block"], t["steps_per_launch"]) in [(w, s) for w, s, _ in t["tried"]]
+    assert (t["warps_per_walker"], t["steps_per_launch"]) in [(w, s) for w, s, _ in t["tried"]]
     after = [(c.walkers(nw)[0], c.accumulators(G)) for c, nw in zip(ctxs, walkers)]
     for (da, aa), (db, ab) in zip(before, after):
         assert np.array_equal(da, db)
@@ -133,7 +148,7 @@ def test_tuner_leaves_state_unchanged_and_sets_a_tried_configuration():
             assert np.array_equal(aa[key], ab[key])
     # the tuned configuration continues the same trajectories
     for c in ctxs:
-        c.set_launch(t["warps_per_block"], t["steps_per_launch"], True)
+        c.set_launch(t["warps_per_walker"], t["steps_per_launch"], True)
     P.batch_advance(ctxs, 10)
     tuned = [c.walkers(nw)[0] for c, nw in zip(ctxs, walkers)]
     for c, nw in zip(ctxs, walkers):

@@ -187,7 +187,8 @@ def test_errors_are_reported():
 
 def test_full_size_launch_sampled_walkers_and_dets():
     """56-orbital CAS(10e,10o) workload in the benchmark's launch configuration (4096 walkers, one
-    walker step per launch): sampled walkers' trajectories and local quantities against the oracle."""
+    walker step per launch): sampled walkers' trajectories, and every per-neighbour record at the
+    start determinant and at one determinant of each class the walkers reached, against the oracle."""
     P = _mrq()
     s = S.workload("cas10_56o")
     ctx = P.Context.from_system(s)
@@ -202,12 +203,17 @@ def test_full_size_launch_sampled_walkers_and_dets():
     for w in (0, 4095):
         traj = orc.walk_one(w, steps, seed)
         assert np.array_equal(dets[w], traj[-1]), w
-    # local quantities at the start determinant and at one FOIS neighbour of it
-    r = orc.local(s.dets[orc.start], max_nb=1)
-    loc, _ = ctx.debug_local(s.dets[orc.start][None])
-    for key_g, key_o in (("S", "S"), ("e_local", "EL"), ("h_nn", "Hnn"), ("psi", "psi")):
-        assert close(loc[key_g][0], r[key_o]), key_g
-    assert loc["n_neighbours"][0] == r["nnb"] and loc["n_terms"][0] == r["terms"]
+    # every neighbour record, element by element, at the start determinant (3.45e5 neighbours)
+    # and at one walker determinant of each class the walk has reached
+    loc, _ = ctx.debug_local(dets)
+    picks, seen = [s.dets[orc.start]], {0}
+    for i in range(nw):
+        t = int(loc["type"][i])
+        if t not in seen:
+            seen.add(t)
+            picks.append(dets[i])
+    assert len(picks) >= 3
+    compare_local(ctx, orc, np.array(picks), s.W)
 
 
 def test_target_sigma_stops_early_and_equals_a_fixed_length_run(tiny_pair):
@@ -217,10 +223,10 @@ def test_target_sigma_stops_early_and_equals_a_fixed_length_run(tiny_pair):
     res = ctx.sample(p)
     steps = res["total_steps"] // 512
     assert res["e2_sigma"] <= 2e-3 and steps < 4000 and steps % 40 == 0
-    ref = ctx.sample(ctx.params(512, steps, burn_in=20, seed=31, n_groups=16, walkers_per_block=2))
+    ref = ctx.sample(ctx.params(512, steps, burn_in=20, seed=31, n_groups=16, warps_per_walker=2))
     for k in ("e2", "e2_sigma", "e_var", "a0sq"):
         assert close(res[k], ref[k], 1e-9), k
-    ctx.walkers_init(ctx.params(32, 0, walkers_per_block=4))
+    ctx.walkers_init(ctx.params(32, 0, warps_per_walker=4))
 
 
 def test_frozen_core_variant_within_3_sigma_of_brute_force(tiny_pair):
@@ -237,3 +243,20 @@ def test_frozen_core_variant_within_3_sigma_of_brute_force(tiny_pair):
         ctx.set_coeffs(s.c)
     assert np.all(res["type_steps"][3:] == 0) and np.all(res["type_e2"][3:] == 0)
     assert abs(res["e2"] - e2_frozen) < 3 * res["e2_sigma"]
+
+
+def test_l2_window_changes_nothing(tiny_pair):
+    """The persisting-L2 window on the integral tables is a cache hint: the same trajectories and
+    the same accumulators, bit for bit."""
+    s, ctx, orc = tiny_pair
+    ctx.set_coeffs(s.c)
+    out = []
+    for frac in (0.0, 1.0):
+        ctx.set_l2_window(frac)
+        ctx.walkers_init(ctx.params(256, 0, burn_in=2, seed=17, n_groups=4))
+        ctx.walkers_advance(12)
+        out.append((ctx.walkers(256)[0], ctx.accumulators(4)))
+    ctx.set_l2_window(0.0)
+    assert np.array_equal(out[0][0], out[1][0])
+    for key in ("N", "U", "W", "E", "type_steps"):
+        assert np.array_equal(out[0][1][key], out[1][1][key]), key

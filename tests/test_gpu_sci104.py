@@ -48,8 +48,8 @@ def test_setup_parity(c3):
     assert info["start"] == orc.start
 
 
-def test_local_quantities_every_class(c3):
-    s, ctx, orc = c3
+def _class_dets(s, orc):
+    """The CAS start determinant and one FOIS determinant of each of the eight classes."""
     n, W, nc, na = s.n_orb, s.W, s.n_core, s.n_act
     start = s.dets[orc.start]
 
@@ -74,7 +74,12 @@ def test_local_quantities_every_class(c3):
         [(0, 1, aemp[1]), (0, 6, v0 + 70)],                      # (2,1)
     ):
         dets.append(_move(start, W, n, moves))
-    dets = np.array(dets)
+    return np.array(dets)
+
+
+def test_local_quantities_every_class(c3):
+    s, ctx, orc = c3
+    dets = _class_dets(s, orc)
     loc, _ = ctx.debug_local(dets)
     types = []
     for i, d in enumerate(dets):
@@ -86,6 +91,30 @@ def test_local_quantities_every_class(c3):
                        ("psi", "psi")):
             assert close(loc[kg][i], r[ko]), (i, kg, loc[kg][i], r[ko])
     assert sorted(types) == [0, 1, 2, 3, 4, 5, 6, 7, 8]
+
+
+def test_per_neighbour_records_at_every_class(c3):
+    """Every neighbour record at full size: at the CAS start determinant (3.2 million neighbours)
+    and one determinant of each FOIS class, the set of excitations is bit-exact against the
+    oracle's enumeration, and a seeded random sample of up to 50,000 records per determinant
+    (images, H_nm, (H_D)_nm, O(m), psi_s(m), Gamma) matches the oracle's evaluation of the same
+    neighbours within 1e-10."""
+    s, ctx, orc = c3
+    dets = _class_dets(s, orc)
+    rng = np.random.default_rng(104)
+    loc, _ = ctx.debug_local(dets)
+    for i, d in enumerate(dets):
+        nnb = int(loc["n_neighbours"][i])
+        _, nb = ctx.debug_local(d[None], max_nb=nnb)
+        g = nb[0]
+        ids = orc.neighbour_ids(d)
+        assert len(ids) == nnb, i
+        assert np.array_equal(np.sort(g["exc"]), np.sort(ids)), i
+        pick = np.sort(rng.choice(nnb, min(nnb, 50_000), replace=False))
+        r = orc.neighbours(d, g["exc"][pick])
+        assert np.array_equal(g["det"][pick][:, :2 * s.W], r["dets"]), i
+        for fg, fo in (("h", "H"), ("hd", "HD"), ("o", "O"), ("psi", "psi_m"), ("gamma", "Gamma")):
+            assert close(g[fg][pick], r[fo]), (i, fg)
 
 
 def test_walk_16384_walkers_sampled_trajectories(c3):

@@ -1,10 +1,12 @@
 """Serving form: requests for different systems admitted by a device-memory budget and advanced
-together (continuous batching) give the same results as each request run alone."""
+together (continuous batching) give the same results as each request run alone (bit for bit) and
+as the oracle's walk of the same request (within 1e-10)."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle as O
 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -37,13 +39,18 @@ def test_served_results_equal_alone():
         srv.step()
         if all(srv.poll(t)["state"] in ("done", "failed") for t in tickets):
             break
-    for t, ref in zip(tickets, alone):
+    for t, ref, s, nw, seed in zip(tickets, alone, systems, walkers, seeds):
         st = srv.poll(t)
         assert st["state"] == "done" and st["steps_done"] == steps
         res = st["result"]
         assert np.array_equal(res["type_steps"], ref["type_steps"])
         for k in ("e2", "e2_sigma", "e_var", "a0sq"):
-            assert _close(res[k], ref[k]), k
+            assert res[k] == ref[k], k
+        orc = O.Oracle.from_system(s)
+        fo = orc.finalize(orc.sample(nw, steps, 2, seed, 8))
+        assert np.array_equal(res["type_steps"], fo["type_steps"])
+        for k in ("e2", "e2_sigma", "e_var", "a0sq"):
+            assert _close(res[k], fo[k], 1e-9), k
     assert srv.info()["active"] == 0 and srv.info()["bytes"] == 0
     srv.close()
 

@@ -44,3 +44,33 @@ def test_noalloc_finalize_matches_finalize_on_two_calls():
         assert g["walker_steps"] == r["walker_steps"] > 0
         assert g["status"] == 0
     ctx.close()
+
+
+def test_noalloc_finalize_rejects_sizes_beyond_its_fixed_scratch():
+    """A walk whose finalize needs more partial sums than the fixed array holds is refused with
+    MRQ_TOO_LARGE (and a message), nothing is written; the ordinary finalize still works, and a
+    smaller group count fits again (two-word determinants, 1.5 million labels)."""
+    import paper_1909_06935_gb300 as P
+    lib = P.load_library()
+    s = S.make_system(10, 2, 60, 11, 11, rank=40, seed=4242)      # 211 x 7261 labels
+    nchunk = -(-len(s.c) // 8192)
+    assert 65 * nchunk * 45 > P.NOALLOC_SCRATCH_DOUBLES > 17 * nchunk * 45
+    ctx = P.Context.from_system(s)
+    try:
+        ctx.walkers_init(ctx.params(64, 0, burn_in=0, seed=5, n_groups=64))
+        ctx.walkers_advance(2)
+        got = P.Result()
+        assert lib.mrq_finalize_noalloc(ctx._h, ctypes.byref(got)) == -9
+        assert b"fixed" in lib.mrq_last_error(ctx._h)
+        assert got.walker_steps == 0
+        assert ctx.finalize()["walker_steps"] == 128
+        ctx.walkers_init(ctx.params(64, 0, burn_in=0, seed=5, n_groups=16))
+        ctx.walkers_advance(2)
+        ref = P.Result()
+        assert lib.mrq_finalize(ctx._h, ctypes.byref(ref)) == 0
+        assert lib.mrq_finalize_noalloc(ctx._h, ctypes.byref(got)) == 0, lib.mrq_last_error(ctx._h)
+        r, g = ref.as_dict(), got.as_dict()
+        for k in KEYS + ARRAYS:
+            assert _close(g[k], r[k]), (k, g[k], r[k])
+    finally:
+        ctx.close()
