@@ -379,19 +379,19 @@ int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB);
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi);
 
 /*
- * The two clocks of the move race (Sec. II B: the rejection-free continuous-time walk, taken in
- * the first-reaction form of Gillespie's algorithm; each neighbour m draws t = -ln(u)/Gamma_nm
- * and the smallest t wins), for parity tests of the screen that decides which candidates need
- * the exact clock.  For i < n: u = (k53[i] + 1) 2^-53 with k53[i] < 2^53 (the 53 random bits of
- * the walk's Philox4x32-10 draw), exact[i] = -ln(u)/rate[i] in FP64, and screen[i] the FP32
- * clock the walk compares first, formed as the walk forms it: within 1e-6 relative of exact[i]
- * for 1e-30 < rate < 1e30 and clocks above 1e-37, and 0 (which never screens a candidate out)
- * otherwise.  All arrays are n long, host or
- * device memory owned by the caller.  Errors: MRQ_INVALID_ARG (null pointers, n <= 0, a k53
- * with more than 53 bits), MRQ_CUDA_ERROR.
+ * The move race's screen, for parity tests (Sec. II B: the rejection-free continuous-time walk,
+ * taken in the first-reaction form of Gillespie's algorithm; each neighbour m draws the clock
+ * t = -ln(u)/Gamma_nm and the smallest t wins).  The walk evaluates the exact FP64 clock only for
+ * candidates that pass an FP32 screen against the best clock so far.  For i < n: u = (k53[i] + 1)
+ * 2^-53 with k53[i] < 2^53 (the 53 random bits of the walk's Philox4x32-10 draw), exact[i] =
+ * -ln(u)/rate[i] in FP64, and pass[i] = 1 when the screen lets a candidate of rate rate[i] through
+ * against the best clock t_best[i] (infinity: none yet), formed exactly as the walk forms it.  The
+ * screen never rejects a candidate whose exact clock is below t_best[i].  All arrays are n long,
+ * host or device memory owned by the caller.  Errors: MRQ_INVALID_ARG (null pointers, n <= 0, a
+ * k53 with more than 53 bits), MRQ_CUDA_ERROR.
  */
-int mrq_debug_race_clocks(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, float* screen,
-                          double* exact);
+int mrq_debug_race_screen(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, const double* t_best,
+                          uint8_t* pass, double* exact);
 
 /*
  * Persisting-L2 window of this context's walk launches (no counterpart in the paper; a GB300
@@ -435,6 +435,64 @@ int mrq_debug_set_limits(mrq_ctx* ctx, int max_probe, int cand_cap);
  * 4 GiB on `device`, runs for about a tenth of a second.  Errors: MRQ_INVALID_ARG, MRQ_CUDA_ERROR.
  */
 int mrq_probe_peaks(int device, double* out3);
+
+/*
+ * Copy the loaded integrals back (h1: n*n doubles, eri: the 8-fold packed array; either may be
+ * NULL), e.g. after mrq_sci_reference rotated them.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
+ */
+int mrq_read_hamiltonian(mrq_ctx* ctx, double* h1, double* eri);
+
+/* Parameters of mrq_sci_reference. */
+typedef struct {
+    int32_t n_strings;      /* selected occupation strings per spin; the reference holds n_strings^2
+                               determinants (clamped to the string space; at most 4096) */
+    int32_t n_seed_strings; /* strings of lowest one-spin energy whose product space seeds the
+                               selection (clamped to the string space; at most n_strings) */
+    double tol;             /* Davidson residual-norm bound of both solves (> 0) */
+    int32_t max_iter;       /* Davidson iterations per solve (>= 1) */
+    int32_t max_sub;        /* Davidson subspace size before a restart (2..64) */
+    int32_t semicanonical;  /* 1: rotate the core and virtual orbitals so that the generalised Fock
+                               blocks F_cc and F_vv are diagonal, and reload the Hamiltonian */
+    int32_t reserved;
+} mrq_sci_params;
+
+/* What mrq_sci_reference built. */
+typedef struct {
+    double energy;          /* variational energy of phi0 in the selected product space (E_core and
+                               e_core included) */
+    double seed_energy;     /* lowest energy in the seed product space */
+    double residual;        /* Davidson residual norm of phi0 */
+    double fock_offdiag;    /* largest |F_pq|, p != q, inside the core and virtual blocks before the
+                               rotation (0 when semicanonical = 0) */
+    double seconds;         /* wall time of the call */
+    int64_t n_det;          /* determinants loaded as the reference (n_strings^2) */
+    int32_t n_strings, n_seed_strings;   /* as used */
+    int32_t iters_seed, iters;           /* Davidson iterations of the seed and the final solve */
+} mrq_sci_result;
+
+/*
+ * Build the reference phi0 on the device as a heat-bath selected CI of the active space (the
+ * selected-CI reference of Sec. II D; Sz = 0, so n_alpha must equal n_beta) and load it as
+ * mrq_load_reference would.  The Hamiltonian in the active space is the core-averaged one:
+ * E_core + sum_tu h_tu E_tu + 1/2 sum (tu|vw)(E_tu E_vw - delta_uv E_tw), h = h1 + sum_i [2(tu|ii) -
+ * (ti|iu)].  Steps: the n_seed_strings strings of lowest one-spin energy (first on ties) span a seed
+ * product space, whose lowest eigenvector C0 (Davidson) weighs each seed string s by w_s =
+ * (sum_b C0[s,b]^2 + sum_a C0[a,s]^2)/2; every string s' scores max_s |<s'|H1|s>| sqrt(w_s) (H1 the
+ * one-spin part of the Hamiltonian; seeds score infinity); the n_strings best (first on ties) span
+ * the final product space, solved again from the embedded C0.  The sign makes the largest |c|
+ * positive.  Determinant k = a n_strings + b holds alpha string a and beta string b of the
+ * selection (strings in lexicographic order of their sorted orbital lists; bit t = active orbital
+ * t).  With semicanonical = 1 the generalised Fock matrix F_pq = h_pq + sum_i [2(pq|ii) - (pi|iq)] +
+ * sum_tu gamma_tu [(pq|tu) - (pt|uq)/2] of the new reference (gamma its spin-summed active 1-RDM)
+ * is diagonalised in the core and virtual blocks (eigenvalues ascending), h1 and (pq|rs) are
+ * rotated on the device and reloaded (as mrq_load_hamiltonian would; mrq_read_hamiltonian returns
+ * them); the active orbitals, and so phi0, are unchanged.  strings_out (n_strings uint32, or NULL)
+ * receives the selected strings, coeffs_out (n_strings^2 doubles, or NULL) the coefficients.  The
+ * one-spin string space C(n_act, n_alpha - n_core) is limited to 65,536 strings.  Errors:
+ * MRQ_NOT_LOADED, MRQ_INVALID_ARG, MRQ_TOO_LARGE, MRQ_OOM, MRQ_CUDA_ERROR, and those of the loads.
+ */
+int mrq_sci_reference(mrq_ctx* ctx, const mrq_sci_params* p, mrq_sci_result* out, uint32_t* strings_out,
+                      double* coeffs_out);
 
 #ifdef __cplusplus
 }

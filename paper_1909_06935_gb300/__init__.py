@@ -84,6 +84,22 @@ class TuneResult(C.Structure):
                            for i in range(n)])
 
 
+class SciParams(C.Structure):
+    _fields_ = [("n_strings", C.c_int32), ("n_seed_strings", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("max_sub", C.c_int32), ("semicanonical", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class SciResult(C.Structure):
+    _fields_ = [("energy", C.c_double), ("seed_energy", C.c_double), ("residual", C.c_double),
+                ("fock_offdiag", C.c_double), ("seconds", C.c_double), ("n_det", C.c_int64),
+                ("n_strings", C.c_int32), ("n_seed_strings", C.c_int32), ("iters_seed", C.c_int32),
+                ("iters", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MRQError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"mrq error {code}: {msg}")
@@ -133,18 +149,20 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_read_coeffs.argtypes = [P, P]
     lib.mrq_read_gradient_sums.argtypes = [P, P, P]
     lib.mrq_sample_batch.argtypes = [P, C.c_int, P, P]
-    lib.mrq_debug_race_clocks.argtypes = [P, I64, P, P, P, P]
+    lib.mrq_debug_race_screen.argtypes = [P, I64, P, P, P, P, P]
     lib.mrq_set_deadline.argtypes = [P, C.c_double]
     lib.mrq_probe_peaks.argtypes = [C.c_int, P]
     lib.mrq_set_l2_window.argtypes = [P, C.c_double]
     lib.mrq_debug_set_limits.argtypes = [P, C.c_int, C.c_int]
+    lib.mrq_read_hamiltonian.argtypes = [P, P, P]
+    lib.mrq_sci_reference.argtypes = [P, C.POINTER(SciParams), C.POINTER(SciResult), P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
                "mrq_finalize_noalloc", "mrq_batch_advance", "mrq_sample_batch", "mrq_mrci_gradient",
                "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_set_launch",
-               "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers", "mrq_debug_race_clocks",
+               "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers", "mrq_debug_race_screen",
                "mrq_set_deadline", "mrq_debug_set_limits", "mrq_probe_peaks",
-               "mrq_set_l2_window"):
+               "mrq_set_l2_window", "mrq_read_hamiltonian", "mrq_sci_reference"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -362,16 +380,47 @@ class Context:
         """Lower the hash-probe bound and the candidate-list capacity (0 restores the default)."""
         self._check(self._lib.mrq_debug_set_limits(self._h, int(max_probe), int(cand_cap)))
 
-    def race_clocks(self, k53, rate):
-        """The move race's FP32 screening clock and exact FP64 clock for (k53, rate) pairs."""
+    def race_screen(self, k53, rate, t_best):
+        """The move race's FP32 screen (pass flags) and exact FP64 clocks for (k53, rate, best) triples."""
         k = np.ascontiguousarray(k53, np.uint64)
         r = np.ascontiguousarray(rate, np.float64)
-        if k.shape != r.shape:
-            raise ValueError("k53 and rate must have the same shape")
-        scr = np.zeros(k.shape, np.float32)
+        tb = np.ascontiguousarray(t_best, np.float64)
+        if k.shape != r.shape or k.shape != tb.shape:
+            raise ValueError("k53, rate and t_best must have the same shape")
+        ok = np.zeros(k.shape, np.uint8)
         ex = np.zeros(k.shape, np.float64)
-        self._check(self._lib.mrq_debug_race_clocks(self._h, k.size, _addr(k), _addr(r), _addr(scr), _addr(ex)))
-        return scr, ex
+        self._check(self._lib.mrq_debug_race_screen(self._h, k.size, _addr(k), _addr(r), _addr(tb), _addr(ok),
+                                                    _addr(ex)))
+        return ok.astype(bool), ex
+
+    def read_hamiltonian(self):
+        """The loaded integrals (h1 as n x n, the packed eri)."""
+        npair = self.n * (self.n + 1) // 2
+        h1 = np.zeros((self.n, self.n))
+        eri = np.zeros(npair * (npair + 1) // 2)
+        self._check(self._lib.mrq_read_hamiltonian(self._h, _addr(h1), _addr(eri)))
+        return h1, eri
+
+    def sci_reference(self, n_strings, n_seed_strings=256, tol=1e-5, max_iter=80, max_sub=24,
+                      semicanonical=True, want_vectors=True):
+        """Build and load the heat-bath selected-CI reference on the device (mrq_sci_reference).
+        Returns the result fields, plus the selected strings and the coefficients (n_strings^2)
+        when want_vectors."""
+        p = SciParams(int(n_strings), int(n_seed_strings), float(tol), int(max_iter), int(max_sub),
+                      1 if semicanonical else 0, 0)
+        r = SciResult()
+        m = n_strings
+        strs = np.zeros(m, np.uint32) if want_vectors else None
+        cs = np.zeros(m * m) if want_vectors else None
+        self._check(self._lib.mrq_sci_reference(self._h, C.byref(p), C.byref(r),
+                                                _addr(strs) if want_vectors else None,
+                                                _addr(cs) if want_vectors else None))
+        out = r.as_dict()
+        if want_vectors:
+            k = r.n_strings
+            out["strings"] = strs[:k].astype(np.int64)
+            out["coeffs"] = cs[: k * k].reshape(k, k)
+        return out
 
     def walkers(self, n_walkers: int):
         d = np.zeros((n_walkers, 2 * self.W), np.uint64)

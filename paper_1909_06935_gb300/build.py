@@ -7,9 +7,9 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
 SOURCES = [os.path.join(SRC_DIR, "mrq.cu"), os.path.join(SRC_DIR, "mrq_probe.cu"),
-           os.path.join(SRC_DIR, "mrq_server.cpp")]
+           os.path.join(SRC_DIR, "mrq_sci.cu"), os.path.join(SRC_DIR, "mrq_server.cpp")]
 DEPS = SOURCES + [os.path.join(SRC_DIR, "mrq_device.cuh"), os.path.join(SRC_DIR, "mrq_cas.cuh"),
-                  os.path.join(SRC_DIR, "mrq_walk.cuh"),
+                  os.path.join(SRC_DIR, "mrq_walk.cuh"), os.path.join(SRC_DIR, "mrq_internal.h"),
                   os.path.join(os.path.dirname(HERE), "include", "mrq.h")]
 LIB = os.path.join(HERE, "_build", "libmrq.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

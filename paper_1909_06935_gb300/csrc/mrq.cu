@@ -22,6 +22,7 @@
 
 #include "../../include/mrq.h"
 #include "mrq_device.cuh"
+#include "mrq_internal.h"
 
 // ============================================================================ per-warp state
 
@@ -301,6 +302,7 @@ struct WalkSet {
     const long long* offsets;
     int nsys;
     long long nslots;
+    long long max_seg = 0;        // the most slots of one system (host side: sizes the slot sort)
 };
 
 __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, int& sys, long long& local) {
@@ -316,15 +318,9 @@ __device__ __forceinline__ void slot_owner(const WalkSet& ws, long long slot, in
 
 // sort key of a walker slot: system, label, then the active occupation (truncated), and the slot
 template <int W>
-__global__ void k_walker_keys(const WalkSet ws, long long npad, unsigned long long* __restrict__ keys,
-                              unsigned* __restrict__ idx) {
+__global__ void k_walker_keys(const WalkSet ws, unsigned long long* __restrict__ keys) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npad) return;
-    if (i >= ws.nslots) {
-        keys[i] = ~0ull;
-        idx[i] = 0xFFFFFFFFu;
-        return;
-    }
+    if (i >= ws.nslots) return;
     int sys;
     long long local;
     slot_owner(ws, i, sys, local);
@@ -338,21 +334,28 @@ __global__ void k_walker_keys(const WalkSet ws, long long npad, unsigned long lo
     int h, p;
     const long long l = det_label<W>(S, d, h, p);
     const unsigned long long act = hash_key(S, active_bits<W>(S, d[0]), active_bits<W>(S, d[1]));
-    keys[i] = ((unsigned long long)(sys & 0xFFFF) << 48) | ((unsigned long long)(l & 0xFFFFFF) << 24) |
-              (act & 0xFFFFFFull);
-    idx[i] = (unsigned)i;
+    keys[i] = ((unsigned long long)(l & 0xFFFFFF) << 24) | (act & 0xFFFFFFull);
 }
 
-// one-block bitonic sort of (key, index) pairs in shared memory, npad a power of two <= MRQ_SORT_MAX
+// Per-system bitonic sort of the slots by key (ties by slot): block b orders the slots of system b,
+// [offsets[b], offsets[b+1]), in shared memory padded to a power of two; a system with fewer than
+// 64 or more than MRQ_SORT_MAX slots keeps its slot order.  order[] receives global slot numbers.
 #define MRQ_SORT_MAX 16384
-__global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict__ keys, unsigned* __restrict__ idx,
-                                                  int npad) {
+__global__ void __launch_bounds__(1024) k_sort_slots(const unsigned long long* __restrict__ keys,
+                                                     const long long* __restrict__ offsets, unsigned* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char sort_smem[];
+    const long long lo = offsets[blockIdx.x];
+    const int n = (int)(offsets[blockIdx.x + 1] - lo);
+    if (n < 64 || n > MRQ_SORT_MAX) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) order[lo + i] = (unsigned)(lo + i);
+        return;
+    }
+    const int npad = 1 << (32 - __clz(n - 1));
     unsigned long long* sk = reinterpret_cast<unsigned long long*>(sort_smem);
     unsigned* si = reinterpret_cast<unsigned*>(sk + npad);
     for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-        sk[i] = keys[i];
-        si[i] = idx[i];
+        sk[i] = i < n ? keys[lo + i] : ~0ull;
+        si[i] = i < n ? (unsigned)(lo + i) : 0xFFFFFFFFu;
     }
     __syncthreads();
     for (int k = 2; k <= npad; k <<= 1) {
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict
             __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < npad; i += blockDim.x) idx[i] = si[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[lo + i] = si[i];
 }
 
 #include "mrq_walk.cuh"
@@ -716,12 +719,15 @@ __global__ void k_setup_finish(const SysDev* __restrict__ sys, const double* par
     }
 }
 
-// the race's two clocks for given (k, rate) pairs (parity of the move selection's screen)
-__global__ void k_race_clocks(const unsigned long long* __restrict__ k, const double* __restrict__ rate, long long n,
-                              float* __restrict__ screen, double* __restrict__ exact) {
+// the race's screen and exact clock for given (k, rate, best clock) triples (parity of the move
+// selection's screen); the screen takes the FP32 images exactly as the walk forms them
+__global__ void k_race_screen(const unsigned long long* __restrict__ k, const double* __restrict__ rate,
+                              const double* __restrict__ tbest, long long n, unsigned char* __restrict__ pass,
+                              double* __restrict__ exact) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    screen[i] = race_screen(k[i], abs_f32_of(rate[i]));      // as the walk forms it
+    const float btf = isinf(tbest[i]) ? INFINITY : (float)tbest[i];
+    pass[i] = race_may_win(k[i], abs_f32_of(rate[i]), btf) ? 1 : 0;
     exact[i] = race_clock_f64(k[i], rate[i]);
 }
 
@@ -1021,6 +1027,7 @@ struct mrq_ctx {
     unsigned long long* d_sort_keys = nullptr;   // walker-slot ordering by determinant
     unsigned* d_sort_idx = nullptr;
     long long sort_cap = 0;
+    size_t sort_smem = 0;
     double* d_partial = nullptr;
     long long partial_cap = 0;
     mrq_result* d_res = nullptr;
@@ -1198,19 +1205,20 @@ struct WalkLaunch {
     cudaAccessPolicyWindow l2win = {};   // num_bytes 0: no persisting-L2 window
 };
 
-static int walk_sort_prepare(mrq_ctx* ctx, long long nslots) {
-    if (nslots < 64 || nslots > MRQ_SORT_MAX) return 0;
-    long long npad = 1;
-    while (npad < nslots) npad <<= 1;
-    if (npad > ctx->sort_cap) {
+// scratch and shared memory of the per-system slot sort; max_seg = the most slots of one system
+static int walk_sort_prepare(mrq_ctx* ctx, long long nslots, long long max_seg) {
+    if (nslots > ctx->sort_cap) {
         dfree(ctx->d_sort_keys);
         dfree(ctx->d_sort_idx);
-        CK(cudaMalloc(&ctx->d_sort_keys, sizeof(unsigned long long) * npad));
-        CK(cudaMalloc(&ctx->d_sort_idx, sizeof(unsigned) * npad));
-        ctx->sort_cap = npad;
+        CK(cudaMalloc(&ctx->d_sort_keys, sizeof(unsigned long long) * nslots));
+        CK(cudaMalloc(&ctx->d_sort_idx, sizeof(unsigned) * nslots));
+        ctx->sort_cap = nslots;
     }
+    long long npad = 64;
+    while (npad < std::min<long long>(max_seg, MRQ_SORT_MAX)) npad <<= 1;
     const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
-    CK(cudaFuncSetAttribute(k_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    CK(cudaFuncSetAttribute(k_sort_slots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    ctx->sort_smem = ssm;
     return 0;
 }
 
@@ -1239,22 +1247,18 @@ static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int c
     const size_t smem = cta_smem_bytes(nw, cap, gstride);
     const long long nslots = ws.nslots;
     if (!L.captured) {
-        if (int r = walk_sort_prepare(ctx, nslots)) return r;
+        if (int r = walk_sort_prepare(ctx, nslots, ws.max_seg)) return r;
         if (int r = walk_attr_prepare(ctx, W, smem)) return r;
     }
     for (int step = 0; step < nsteps; step++) {
-        const unsigned* order = nullptr;
-        if (nslots >= 64 && nslots <= MRQ_SORT_MAX) {
-            long long npad = 1;
-            while (npad < nslots) npad <<= 1;
-            const unsigned nb = (unsigned)((npad + 255) / 256);
-            if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
-            else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, npad, ctx->d_sort_keys, ctx->d_sort_idx);
-            const size_t ssm = (size_t)npad * (sizeof(unsigned long long) + sizeof(unsigned));
-            k_bitonic<<<1, 1024, ssm, ctx->stream>>>(ctx->d_sort_keys, ctx->d_sort_idx, (int)npad);
-            CK(cudaGetLastError());
-            order = ctx->d_sort_idx;
-        }
+        // order every system's slots by determinant (walkers on one determinant in neighbouring blocks)
+        const unsigned nb = (unsigned)((nslots + 255) / 256);
+        if (W == 1) k_walker_keys<1><<<nb, 256, 0, ctx->stream>>>(ws, ctx->d_sort_keys);
+        else k_walker_keys<2><<<nb, 256, 0, ctx->stream>>>(ws, ctx->d_sort_keys);
+        k_sort_slots<<<(unsigned)ws.nsys, 1024, ctx->sort_smem, ctx->stream>>>(ctx->d_sort_keys, ws.offsets,
+                                                                              ctx->d_sort_idx);
+        CK(cudaGetLastError());
+        const unsigned* order = ctx->d_sort_idx;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)nslots);
         cfg.blockDim = dim3(32 * nw);
@@ -1580,7 +1584,7 @@ int mrq_load_reference(mrq_ctx* ctx, int64_t n_det, const uint64_t* dets, const 
     free_reference(ctx);
     const int W = ctx->W;
     unsigned long long cap = 16;
-    while (cap < 2ull * (unsigned long long)n_det) cap <<= 1;
+    while (cap < 4ull * (unsigned long long)n_det) cap <<= 1;
     ctx->hcap = cap;
     ctx->nref = n_det;
     unsigned long long* d_dets = nullptr;
@@ -1841,6 +1845,7 @@ int mrq_walkers_advance(mrq_ctx* ctx, int64_t n_steps) {
     }
     CK(cudaEventRecord(ctx->evs[k], ctx->stream));
     WalkSet ws{ctx->d_sys, ctx->d_wptr, ctx->d_woff, 1, ctx->nwalk};
+    ws.max_seg = ctx->nwalk;
     WalkLaunch L;
     L.wpb = warps_of(ctx);
     if (int r = l2_window(ctx, L.l2win)) return r;
@@ -2018,6 +2023,7 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
         cap = std::max(cap, ctxs[i]->hsys.cand_cap);
     }
     ws = WalkSet{ctx->d_bsys, ctx->d_bwptr, ctx->d_boff, (int)sys.size(), off.back()};
+    for (size_t k = 0; k + 1 < off.size(); k++) ws.max_seg = std::max(ws.max_seg, off[k + 1] - off[k]);
     gstride = 0;
     for (const SysDev& sd : sys) gstride = std::max(gstride, sd.gstride);
     if (sys.empty()) return 0;
@@ -2038,7 +2044,7 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstrid
     if (spl <= 0 || spl > n_steps) spl = n_steps;
     const int64_t nfull = n_steps / spl, rem = n_steps % spl;
     if (graph && nfull > 0) {
-        if (int r = walk_sort_prepare(ctx, ws.nslots)) return r;
+        if (int r = walk_sort_prepare(ctx, ws.nslots, ws.max_seg)) return r;
         if (int r = walk_attr_prepare(ctx, W, cta_smem_bytes(std::min(wpb, MRQ_MAXNW), cap, gstride))) return r;
         mrq_ctx::GraphKey key;
         key.sys = ws.systems;
@@ -2282,32 +2288,35 @@ int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB) {
     return 0;
 }
 
-int mrq_debug_race_clocks(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, float* screen,
-                          double* exact) {
+int mrq_debug_race_screen(mrq_ctx* ctx, int64_t n, const uint64_t* k53, const double* rate, const double* t_best,
+                          uint8_t* pass, double* exact) {
     if (!ctx) return MRQ_INVALID_ARG;
     ctx->err[0] = 0;
-    if (n <= 0 || !k53 || !rate || !screen || !exact) return fail(ctx, MRQ_INVALID_ARG, "bad arguments");
+    if (n <= 0 || !k53 || !rate || !t_best || !pass || !exact) return fail(ctx, MRQ_INVALID_ARG, "bad arguments");
     for (int64_t i = 0; i < n; i++)
         if (k53[i] >= (1ull << 53)) return fail(ctx, MRQ_INVALID_ARG, "k53[%lld] has more than 53 bits", (long long)i);
     CK(cudaSetDevice(ctx->device));
     unsigned long long* d_k = nullptr;
-    double *d_r = nullptr, *d_e = nullptr;
-    float* d_s = nullptr;
+    double *d_r = nullptr, *d_t = nullptr, *d_e = nullptr;
+    unsigned char* d_p = nullptr;
     CK(cudaMalloc(&d_k, sizeof(unsigned long long) * n));
     CK(cudaMalloc(&d_r, sizeof(double) * n));
+    CK(cudaMalloc(&d_t, sizeof(double) * n));
     CK(cudaMalloc(&d_e, sizeof(double) * n));
-    CK(cudaMalloc(&d_s, sizeof(float) * n));
+    CK(cudaMalloc(&d_p, n));
     CK(cudaMemcpyAsync(d_k, k53, sizeof(unsigned long long) * n, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemcpyAsync(d_r, rate, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
-    k_race_clocks<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(d_k, d_r, n, d_s, d_e);
+    CK(cudaMemcpyAsync(d_t, t_best, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    k_race_screen<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(d_k, d_r, d_t, n, d_p, d_e);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(screen, d_s, sizeof(float) * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(pass, d_p, n, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemcpyAsync(exact, d_e, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
-    if (int r_ = sync_stream(ctx)) return r_;
+    CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(d_k);
     cudaFree(d_r);
+    cudaFree(d_t);
     cudaFree(d_e);
-    cudaFree(d_s);
+    cudaFree(d_p);
     return 0;
 }
 
@@ -2348,6 +2357,7 @@ int mrq_phase_times(unsigned long long* out10) {
 }
 #endif
 
+
 int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
     if (!ctx) return MRQ_INVALID_ARG;
     if (!ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
@@ -2368,4 +2378,36 @@ int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
     return 0;
 }
 
+int mrq_read_hamiltonian(mrq_ctx* ctx, double* h1, double* eri) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ham) return fail(ctx, MRQ_NOT_LOADED, "no Hamiltonian loaded");
+    CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
+    if (h1) CK(cudaMemcpyAsync(h1, ctx->d_h1, sizeof(double) * ctx->n * ctx->n, cudaMemcpyDefault, ctx->stream));
+    if (eri) CK(cudaMemcpyAsync(eri, ctx->d_eri, sizeof(double) * ctx->neri, cudaMemcpyDefault, ctx->stream));
+    return sync_stream(ctx);
+}
+
 }  // extern "C"
+
+int mrq_internal_ham(mrq_ctx* ctx, MrqHamView* out) {
+    if (!ctx->ham) return fail(ctx, MRQ_NOT_LOADED, "load the Hamiltonian first");
+    ctx->err[0] = 0;
+    *out = MrqHamView{ctx->device, ctx->stream, ctx->n, ctx->nc, ctx->na, ctx->nv, ctx->nalpha, ctx->nbeta, ctx->W,
+                      ctx->d_h1, ctx->d_eri, ctx->neri, ctx->e_nuc};
+    return 0;
+}
+
+int mrq_internal_fail(mrq_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int mrq_internal_sync(mrq_ctx* ctx) { return sync_stream(ctx); }
+

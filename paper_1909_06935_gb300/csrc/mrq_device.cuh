@@ -205,6 +205,7 @@ __device__ __forceinline__ double hash_lookup(const SysDev& S, unsigned long lon
     return hash_lookup(S, key, c);
 }
 
+
 // ------------------------------------------------------------------ labels
 
 __device__ __forceinline__ long long set_rank(int cnt, int x0, int x1, int m) {
@@ -543,17 +544,16 @@ __device__ __forceinline__ float abs_f32_of(double x) {
     return __uint_as_float(f);
 }
 
-// The race clock -ln(u)/Gamma in FP32, for screening only, from the FP32 image gf of Gamma.  For
-// u < 1/2 it is -ln(u) from u itself (u = (k+1) 2^-53 rounds to FP32 with relative error 6e-8 and
-// never underflows); for u >= 1/2 it is -log1p(-(1-u)) with 1-u = (2^53-k-1) 2^-53 (< 2^52, rounded
-// once), so the clock's relative error stays below 1e-6 for every k.  0 - which never screens a
-// candidate out, the exact FP64 clock then decides - when gf is outside [1e-30, 1e30] or the clock
-// itself falls below the normal FP32 range.
-__device__ __forceinline__ float race_screen(unsigned long long k, float gf) {
-    if (!(gf > 1e-30f && gf < 1e30f)) return 0.0f;
-    float lnu;
-    if (k < 4503599627370495ull) lnu = logf((float)(k + 1ull) * 1.1102230246251565e-16f);
-    else lnu = log1pf(-(float)(9007199254740991ull - k) * 1.1102230246251565e-16f);
-    const float t = -lnu / gf;
-    return t < 1e-37f ? 0.0f : t;
+// The race's screen: can a neighbour with rate Gamma (FP32 image gf) and random bits k beat the best
+// clock t_best so far (FP32 image btf)?  Its exact clock -ln(u)/Gamma wins iff u > exp(-Gamma t_best),
+// i.e. iff w = 1 - u = (2^53 - 1 - k) 2^-53 < -expm1(-Gamma t_best).  With y = gf btf (1 + 1e-4),
+// which exceeds Gamma t_best despite the FP32 roundings, and y <= 4, the test w < -expm1(-y) has
+// a relative margin above 1.8e-6, far above the FP32 errors (about 2e-7), so it never rejects a
+// winner; for y > 4, for gf, btf or y outside the normal FP32 range and with no best yet it lets every
+// candidate through, and the exact FP64 clock decides.  No logarithm and no division per neighbour.
+__device__ __forceinline__ bool race_may_win(unsigned long long k, float gf, float btf) {
+    if (!(gf >= 1e-30f) || !(btf >= 1e-30f)) return true;
+    const float y = gf * btf * 1.0001f;
+    if (!(y >= 1e-30f && y <= 4.0f)) return true;
+    return (float)(9007199254740991ull - k) * 1.1102230246251565e-16f < -expm1f(-y);
 }

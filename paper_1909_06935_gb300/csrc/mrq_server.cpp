@@ -60,7 +60,7 @@ int64_t footprint_of(const Request& r) {
     const int64_t nlab = (1 + 2 * (int64_t)r.n_core + nsub2(2 * r.n_core)) *
                          (1 + 2 * (int64_t)r.n_virt + nsub2(2 * r.n_virt));
     int64_t cap = 16;
-    while (cap < 2 * (int64_t)r.coeffs.size()) cap <<= 1;
+    while (cap < 4 * (int64_t)r.coeffs.size()) cap <<= 1;
     const int64_t G = std::max<int32_t>(r.params.n_groups, 1);
     int64_t b = 0;
     const int64_t nca = r.n_core + r.n_act, nav = r.n_act + r.n_virt;

@@ -18,8 +18,8 @@
 //
 // The per-neighbour arithmetic is kept to a few FP64 operations: t = H_nm psi_s(m) is summed as
 // |t| and t, and 1/psi_s(n) is applied once per walker (S = |1/psi_n| sum |t|, E_L = H_nn +
-// (1/psi_n) sum t); the race screens candidates with an FP32 clock built by integer operations and
-// takes the exact FP64 clock only where a candidate can win.
+// (1/psi_n) sum t); the race screens candidates in FP32 (no logarithm: 1 - u against
+// -expm1(-Gamma t_best)) and takes the exact FP64 clock only where a candidate can win.
 
 #ifndef MRQ_MAXNW
 #define MRQ_MAXNW 8           // warps per walker block (at most)
@@ -27,7 +27,7 @@
 #define MRQ_VW 8              // virtual warps: the fixed partition of a walker's units (MRQ_MAXNW <= MRQ_VW)
 #define MRQ_CAS_CH 128        // neighbours per unit inside the CAS
 #define MRQ_FOIS_CH 128       // neighbours per unit of a FOIS walker
-#define MRQ_UNIT_NB 512       // neighbours per unit of an (X_a, Y_a) pair (pairs are cut into chunks)
+#define MRQ_UNIT_NB 1024      // neighbours per unit of an (X_a, Y_a) pair (pairs are cut into chunks)
 #ifndef MRQ_WALK_MINB
 #define MRQ_WALK_MINB 2       // walk blocks of MRQ_MAXNW warps resident per SM (bounds the registers)
 #endif
@@ -87,6 +87,9 @@ __device__ __forceinline__ void acc2_init(LaneAcc2& a) {
     a.bpsi = 0.0;
 }
 
+// the exact FP64 clock, kept out of the hot loop's code (few candidates pass the screen)
+__device__ __noinline__ double race_clock_cold(unsigned long long k53, double g) { return race_clock_f64(k53, g); }
+
 // one neighbour m: sums and the race (Sec. II B first-reaction form).  t = H_nm psi_s(m).
 template <int MODE>
 __device__ __forceinline__ void lane_post2(const SysDev& S, LaneAcc2& a, double t, double tD, double psim,
@@ -96,14 +99,12 @@ __device__ __forceinline__ void lane_post2(const SysDev& S, LaneAcc2& a, double 
     a.sT += t;
     a.sD += tD;
     if (MODE == MODE_STEP) {
-        const float gf = abs_f32_of(t) * inv_psin_f;
         if ((__double_as_longlong(t) << 1) != 0) {          // t != 0, without an FP64 compare
             const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
-            const float tf = race_screen(k53, gf);
-            if (!(tf > a.btf * 1.0001f)) {
+            if (race_may_win(k53, abs_f32_of(t) * inv_psin_f, a.btf)) {
                 const double g = fabs(t * inv_psin);
                 if (g > 0.0) {
-                    const double tc = race_clock_f64(k53, g);
+                    const double tc = race_clock_cold(k53, g);
                     if (tc < a.bt || (tc == a.bt && exc < a.bexc)) {
                         a.bt = tc;
                         a.btf = (float)tc;

@@ -1,52 +1,63 @@
 """The move race's FP32 screen never drops the winner (Sec. II B, first-reaction form).
 
 The walk draws an exponential clock t = -ln(u)/Gamma for every neighbour and moves to the
-smallest.  It evaluates the exact FP64 clock only for candidates whose FP32 clock is within a
-1e-4 margin of the best so far, so the FP32 clock (formed exactly as the walk forms it, from the
-FP32 image of Gamma) must track the FP64 one to well under 1e-4 for every u, including u near 0
-(k small) and near 1 (k near 2^53), and must be 0 - never screened out - wherever FP32 cannot
-hold it: rates outside [1e-30, 1e30] and clocks below the normal FP32 range.
+smallest.  It takes the exact FP64 clock only for candidates that pass an FP32 screen against the
+lane's best clock so far (u > exp(-Gamma t_best), tested as 1 - u < -expm1(-y) with a 1e-4 margin
+on y).  The screen must let through every candidate whose exact clock beats the best, for every u
+(u near 0 and near 1 included), and must reject clear losers, so that it does its job.
 """
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
-KS = [0, 1, 2, 1 << 20, (1 << 28) - 1, 1 << 28, 1 << 36, 1 << 45, (1 << 52) - 2, (1 << 52) - 1, 1 << 52,
-      (1 << 52) + 1, 1 << 51, (1 << 53) - 2, (1 << 53) - 1]
+KS = [0, 1, 2, 1 << 20, (1 << 28) - 1, 1 << 28, 1 << 36, 1 << 45, (1 << 51), (1 << 52) - 2, (1 << 52) - 1,
+      1 << 52, (1 << 52) + 1, (1 << 53) - 2, (1 << 53) - 1]
 RATES = [1e-29, 1e-10, 3.7e-3, 1.0, 42.0, 1e10, 1e29]
+FACTORS = [0.25, 0.5, 0.9, 0.999, 0.99999, 1.00001, 1.0001, 1.001, 1.1, 2.0, 10.0, 1e6]
 
 
-def _clocks(k, r):
+def _screen(k, r, tb):
     import paper_1909_06935_gb300 as P
     with P.Context() as ctx:
-        return ctx.race_clocks(k, r)
+        return ctx.race_screen(k, r, tb)
 
 
-def test_screen_tracks_the_exact_clock_for_every_u():
+def _grid():
     rng = np.random.default_rng(5)
-    ks = np.array(KS + list(rng.integers(0, 1 << 53, 2000, dtype=np.uint64)), np.uint64)
+    ks = np.array(KS + list(rng.integers(0, 1 << 53, 600, dtype=np.uint64)), np.uint64)
     k, r = np.meshgrid(ks, np.array(RATES))
     k, r = k.ravel(), r.ravel()
-    scr, ex = _clocks(k, r)
-    u = (k.astype(np.float64) + 1.0) * 2.0 ** -53          # exact: k + 1 <= 2^53
-    ref = -np.log(u) / r
-    assert np.allclose(ex, ref, rtol=1e-15, atol=0.0)
-    assert np.all(np.isfinite(scr)) and np.all(np.isfinite(ex)) and np.all(scr >= 0.0)
-    # the safety property: the screen never exceeds the exact clock by more than 1e-6
-    assert np.all(scr.astype(np.float64) <= ex * (1.0 + 1e-6))
-    # 0 only where FP32 cannot hold the clock (u = 1, or a clock below the normal FP32 range)
-    zero = scr == 0.0
-    assert np.all((ex[zero] == 0.0) | (ex[zero] < 1.2e-37))
-    rel = np.abs(scr[~zero].astype(np.float64) / ex[~zero] - 1.0)
-    assert rel.max() < 1e-6, (rel.max(), k[~zero][rel.argmax()], r[~zero][rel.argmax()])
-    # the screen is exercised, not bypassed: almost every pair gets a finite FP32 clock
-    assert (~zero).mean() > 0.99
+    exact = -np.log((k.astype(np.float64) + 1.0) * 2.0 ** -53) / r
+    return k, r, exact
 
 
-def test_rates_outside_the_fp32_range_are_never_screened_out():
-    k = np.array([0, 1 << 30, (1 << 53) - 2, 12345, 1 << 52], np.uint64)
-    r = np.array([1e-300, 1e-40, 1e-31, 1e31, 1e300])
-    scr, ex = _clocks(k, r)
-    assert np.all(scr == 0.0)
-    assert np.allclose(ex, -np.log((k.astype(np.float64) + 1.0) * 2.0 ** -53) / r, rtol=1e-15)
+def test_screen_never_rejects_a_winner():
+    k, r, exact = _grid()
+    kk, rr, tb = [], [], []
+    for f in FACTORS:
+        kk.append(k)
+        rr.append(r)
+        tb.append(np.where(exact > 0, exact * f, 1e-300 * f))
+    kk, rr, tb = np.concatenate(kk), np.concatenate(rr), np.concatenate(tb)
+    ok, ex = _screen(kk, rr, tb)
+    assert np.allclose(ex, -np.log((kk.astype(np.float64) + 1.0) * 2.0 ** -53) / rr, rtol=1e-15, atol=0.0)
+    wins = ex < tb
+    assert wins.sum() > 1000
+    assert np.all(ok[wins]), (kk[wins & ~ok][:5], rr[wins & ~ok][:5], tb[wins & ~ok][:5])
+    # clear losers (clock at least 10 % above the best) are rejected wherever the screen is active:
+    # rate, best clock and their product in the normal FP32 range, Gamma t_best <= 3.9
+    active = (rr >= 1e-29) & (rr <= 1e29) & (tb >= 1e-29) & (tb <= 1e29) & (rr * tb >= 1e-29) & (rr * tb <= 3.9)
+    losers = active & (ex > 1.1 * tb)
+    assert losers.sum() > 1000
+    assert not np.any(ok[losers])
+
+
+def test_no_best_yet_and_rates_outside_the_fp32_range_always_pass():
+    k, r, exact = _grid()
+    ok, _ = _screen(k, r, np.full(len(k), np.inf))
+    assert np.all(ok)
+    k2 = np.array([0, 1 << 30, (1 << 53) - 2, 12345, 1 << 52], np.uint64)
+    r2 = np.array([1e-300, 1e-40, 1e-31, 1e31, 1e300])
+    ok2, _ = _screen(k2, r2, np.full(5, 1.0))
+    assert np.all(ok2)
