@@ -205,8 +205,9 @@ __global__ void k_sci_rank_select(const double* __restrict__ key, long long n, l
     if (i < n) sel[i] = before < k ? 1 : 0;
 }
 
-// ordered compaction of the flagged indices (one block): out[c] = c-th flagged index, *count
-__global__ void k_sci_compact(const unsigned char* __restrict__ flag, long long n, int* __restrict__ out,
+// ordered compaction of the flagged indices (one block): out[c] = c-th flagged index for c < cap,
+// *count = number flagged
+__global__ void k_sci_compact(const unsigned char* __restrict__ flag, long long n, int* __restrict__ out, int cap,
                               int* __restrict__ count) {
     __shared__ long long part[1024];
     const long long per = (n + blockDim.x - 1) / blockDim.x;
@@ -227,7 +228,10 @@ __global__ void k_sci_compact(const unsigned char* __restrict__ flag, long long 
     __syncthreads();
     long long pos = part[threadIdx.x];
     for (long long i = lo; i < hi; i++)
-        if (flag[i]) out[pos++] = (int)i;
+        if (flag[i]) {
+            if (pos < cap) out[pos] = (int)i;
+            pos++;
+        }
 }
 
 // ---------------------------------------------------------------------------- product space
@@ -494,7 +498,8 @@ __global__ void k_sci_embed(const double* __restrict__ C0, int m0, const int* __
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)m0 * m0) return;
     const int a = (int)(i / m0), b = (int)(i % m0);
-    X[(long long)map[seed_sel[a]] * m + map[seed_sel[b]]] = C0[i];
+    const int pa = map[seed_sel[a]], pb = map[seed_sel[b]];
+    if (pa >= 0 && pb >= 0) X[(long long)pa * m + pb] = C0[i];
 }
 
 // ---------------------------------------------------------------------------- reference outputs
@@ -833,6 +838,7 @@ struct SciRun {
                     Hs[(size_t)i * k + j] = 0.5 * (M[(size_t)i * max_sub + j] + M[(size_t)j * max_sub + i]);
             jacobi_eigh(k, Hs, w, U);
             e = w[0];
+            if (!std::isfinite(e)) return mrq_internal_fail(ctx, MRQ_CUDA_ERROR, "Davidson reached a non-finite energy");
             for (int i = 0; i < k; i++) c[i] = U[(size_t)i * k];
             if (int q = combine(V, N, k, c.data(), 0.0, x)) return q;
             if (int q = combine(AV, N, k, c.data(), 0.0, ax)) return q;
@@ -943,8 +949,12 @@ extern "C" int mrq_sci_reference(mrq_ctx* ctx, const mrq_sci_params* p, mrq_sci_
     SCK(buf.get(d_idx, 1));
     const unsigned rbl = (unsigned)((nstr + 255) / 256);
     k_sci_rank_select<<<rbl, 256, 256 * sizeof(double), st>>>(hd, nstr, nseed, 0, flag);
-    k_sci_compact<<<1, 1024, 0, st>>>(flag, nstr, seed_sel, d_count);
+    k_sci_compact<<<1, 1024, 0, st>>>(flag, nstr, seed_sel, nseed, d_count);
     SCK(cudaGetLastError());
+    int count = 0;
+    SCK(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    if (count != nseed) return mrq_internal_fail(ctx, MRQ_CUDA_ERROR, "seed selection found %d strings", count);
     Space S0;
     if (int r = R.build_space(seed_sel, nseed, S0)) return r;
     const long long N0 = (long long)nseed * nseed;
@@ -970,8 +980,12 @@ extern "C" int mrq_sci_reference(mrq_ctx* ctx, const mrq_sci_params* p, mrq_sci_
     k_sci_weights<<<(nseed + 127) / 128, 128, 0, st>>>(C0, nseed, sw);
     k_sci_score<<<rbl, 256, 0, st>>>(T, strs, nstr, S0.sstr, S0.map, sw, nseed, score);
     k_sci_rank_select<<<rbl, 256, 256 * sizeof(double), st>>>(score, nstr, nsel, 1, flag);
-    k_sci_compact<<<1, 1024, 0, st>>>(flag, nstr, sel, d_count);
+    k_sci_compact<<<1, 1024, 0, st>>>(flag, nstr, sel, nsel, d_count);
     SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(&count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    if (count != nsel)
+        return mrq_internal_fail(ctx, MRQ_CUDA_ERROR, "selection found %d strings (scores not finite?)", count);
     Space S1;
     if (int r = R.build_space(sel, nsel, S1)) return r;
     const long long N1 = (long long)nsel * nsel;

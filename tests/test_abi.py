@@ -46,13 +46,13 @@ def test_ctypes_layouts_match_the_c_header(tmp_path):
     """Compile a C program against include/mrq.h and compare struct sizes with the binding's."""
     import subprocess
     src = tmp_path / "sizes.c"
-    src.write_text('#include <stdio.h>\n#include "mrq.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    src.write_text('#include <stdio.h>\n#include "mrq.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    ' sizeof(mrq_sample_params), sizeof(mrq_result), sizeof(mrq_local), sizeof(mrq_neighbour),'
                    ' sizeof(mrq_server_params), sizeof(mrq_request), sizeof(mrq_request_status),'
-                   ' sizeof(mrq_tune_result)); return 0;}\n')
+                   ' sizeof(mrq_tune_result), sizeof(mrq_sci_params), sizeof(mrq_sci_result)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(t) for t in (P.SampleParams, P.Result, P.Local, P.Neighbour, P.ServerParams, P.Request,
-                                       P.RequestStatus, P.TuneResult)]
+                                       P.RequestStatus, P.TuneResult, P.SciParams, P.SciResult)]
     assert got == want

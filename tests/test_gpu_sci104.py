@@ -129,3 +129,30 @@ def test_walk_16384_walkers_sampled_trajectories(c3):
     for w in (0, nw - 1):
         traj = orc.walk_one(w, steps, seed)
         assert np.array_equal(dets[w], traj[-1]), w
+
+
+def test_device_selected_ci_reproduces_the_host_reference(c3):
+    """The device generator (mrq_sci_reference) on the raw 104-orbital integrals selects the host
+    generator's 1,000 strings and reaches its energy; the semicanonical rotation it loads gives the
+    same E0 and core/virtual orbital energies as the host's rotated integrals."""
+    import time
+    import paper_1909_06935_gb300 as P
+    s, ctx_host, _ = c3
+    h1, L = S.make_integrals(10, 14, 80, 312, 2309, chol_sigma=0.05)
+    alpha = np.unique((s.dets[:, 0] >> np.uint64(10)) & np.uint64((1 << 14) - 1)).astype(np.int64)
+    ctx = P.Context()
+    try:
+        ctx.load_hamiltonian(10, 14, 80, 17, 17, h1, S.pack_eri(L), s.e_nuc)
+        t0 = time.perf_counter()
+        r = ctx.sci_reference(1000, n_seed_strings=256, tol=1e-5, max_iter=80, max_sub=24, semicanonical=True)
+        dt = time.perf_counter() - t0
+        info = ctx.setup_info()
+    finally:
+        ctx.close()
+    print(f"device selected CI: {dt:.2f} s, E = {r['energy']:.12f}, iterations {r['iters_seed']} + {r['iters']}")
+    assert r["n_det"] == 1_000_000
+    assert sorted(r["strings"].tolist()) == alpha.tolist()
+    assert abs(r["energy"] - s.e_cas) < 1e-7
+    ref = ctx_host.setup_info()
+    assert abs(info["e0"] - ref["e0"]) < 1e-7
+    assert np.allclose(info["eps"], ref["eps"], atol=1e-7)
