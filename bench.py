@@ -138,6 +138,42 @@ def max_over_ranks(ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def groups_per_rank(world: int) -> int:
+    """Walker groups of each rank: 16, fewer when all ranks' groups together would exceed the 64 a
+    context can finalize."""
+    return max(1, min(16, 64 // max(world, 1)))
+
+
+def merge_rank_accumulators(accs):
+    """Union of the ranks' walker groups (rank r's group g becomes group r G + g): the per-group
+    sums are concatenated, the type counts and walker steps add up."""
+    out = {k: np.concatenate([np.asarray(a[k]) for a in accs], 0)
+           for k in ("N", "U", "W", "E", "A", "B") if all(a.get(k) is not None for a in accs)}
+    out["type_steps"] = np.sum([np.asarray(a["type_steps"]) for a in accs], 0).astype(np.int64)
+    out["total_steps"] = int(sum(int(a.get("total_steps", 0)) for a in accs))
+    return out
+
+
+def combine_ranks(ctx, groups: int, world: int, rank: int, total_steps: int):
+    """Every rank's accumulators to rank 0, which finalizes their union (the cross-rank reduction
+    of a multi-process run; one exchange after the timed region)."""
+    acc = ctx.accumulators(groups)
+    acc["A"], acc["B"] = ctx.gradient_sums(groups)
+    acc["total_steps"] = total_steps
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    objs = [None] * world
+    dist.all_gather_object(objs, acc)
+    if rank != 0:
+        return None
+    merged = merge_rank_accumulators(objs)
+    ctx.load_accumulators(merged, merged["total_steps"])
+    res = ctx.finalize()
+    return {"groups": groups * world, "walker_steps": merged["total_steps"], "e2": res["e2"],
+            "e2_sigma": res["e2_sigma"], "e_var": res["e_var"], "e_var_sigma": res["e_var_sigma"]}
+
+
 def job_rate(units_per_rank: float, world: int, ms: float) -> float:
     """Whole-job walker-steps/s: all ranks' units over the slowest rank's time (weak scaling)."""
     return world * units_per_rank / (ms / 1e3)
@@ -245,7 +281,8 @@ def run_ours(args):
     ctx.set_coeffs(system.c)
     nw, inner = args.walkers, args.inner
     seed = rank_seed(rank)
-    p = ctx.params(nw, args.warmup * inner, burn_in=0, seed=seed, n_groups=16)
+    groups = groups_per_rank(world)
+    p = ctx.params(nw, args.warmup * inner, burn_in=0, seed=seed, n_groups=groups)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
     def barrier():
@@ -280,6 +317,7 @@ def run_ours(args):
     walk_s = res["seconds"] - (res_w["seconds"] if res_w else 0.0)
     walk_launches = res["walk_launches"] - (res_w["walk_launches"] if res_w else 0)
     snap1 = ctx.walkers(nw)[0]
+    combined = combine_ranks(ctx, groups, world, rank, int(res["total_steps"]))
     units = nw * inner * args.steps
     value = job_rate(units, world, ms)
 
@@ -380,11 +418,14 @@ def run_ours(args):
                        "orbitals": f"{system.n_core} core, {system.n_act} active, {system.n_virt} virtual",
                        "electrons": system.n_alpha + system.n_beta,
                        "reference_dets": int(len(system.coeffs)), "walkers_per_gpu": nw,
-                       "walker_steps_per_launch": inner, "groups": 16, "method": "SC-NEVPT2(s) + E_L",
+                       "walker_steps_per_launch": inner, "groups": groups, "method": "SC-NEVPT2(s) + E_L",
                        "l2": "256 MB buffer written between timed steps",
                        "neighbours_per_walker_step": nb_per_step, "candidates_per_walker_step": cand_per_step,
                        "class_mix": {P.TYPE_NAMES[t]: int(res["type_steps"][t]) for t in range(P.NTYPES)},
-                       "e2": res["e2"], "e2_sigma": res["e2_sigma"]},
+                       "e2": res["e2"], "e2_sigma": res["e2_sigma"],
+                       # N > 1: the estimate of all ranks' walkers, finalized by rank 0 over the union
+                       # of their groups
+                       "all_ranks": combined},
             "clocks": clk.summary(),
             "roofline": roof,
             "e2e": e2e,

@@ -437,6 +437,22 @@ int mrq_debug_set_limits(mrq_ctx* ctx, int max_probe, int cand_cap);
 int mrq_probe_peaks(int device, double* out3);
 
 /*
+ * Replace this context's accumulators by given per-group sums, e.g. the union of the groups of
+ * several independent walks: the combining step of a run whose ranks each walk their own walkers
+ * (the paper's implementation reduces over MPI ranks of walkers, Sec. III).  A rank reads its
+ * sums with mrq_read_accumulators / mrq_read_gradient_sums; rank 0 concatenates every rank's
+ * groups (rank r's group g becomes group r G + g) and loads them here, and mrq_finalize then
+ * reports the combined estimates with jackknife errors over all n_groups groups.  accN, accU,
+ * accA, accB: n_groups x n_labels row-major (accA, accB may be NULL: zero); accW, accE: n_groups;
+ * type_steps: MRQ_NTYPES counts; total_steps: walker steps of all the walks.  Host or device
+ * memory, copied in.  The context's walkers are left out of step (mrq_walkers_init starts a new
+ * walk).  Errors: MRQ_NOT_LOADED (no reference), MRQ_INVALID_ARG (1 <= n_groups <= 64), MRQ_OOM.
+ */
+int mrq_load_accumulators(mrq_ctx* ctx, int32_t n_groups, const double* accN, const double* accU, const double* accW,
+                          const double* accE, const double* accA, const double* accB, const int64_t* type_steps,
+                          int64_t total_steps);
+
+/*
  * Copy the loaded integrals back (h1: n*n doubles, eri: the 8-fold packed array; either may be
  * NULL), e.g. after mrq_sci_reference rotated them.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
  */

@@ -155,6 +155,7 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_set_l2_window.argtypes = [P, C.c_double]
     lib.mrq_debug_set_limits.argtypes = [P, C.c_int, C.c_int]
     lib.mrq_read_hamiltonian.argtypes = [P, P, P]
+    lib.mrq_load_accumulators.argtypes = [P, C.c_int32, P, P, P, P, P, P, P, I64]
     lib.mrq_sci_reference.argtypes = [P, C.POINTER(SciParams), C.POINTER(SciResult), P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
                "mrq_setup_info", "mrq_debug_local", "mrq_walkers_init", "mrq_walkers_advance", "mrq_finalize",
@@ -162,7 +163,7 @@ def load_library(build_if_missing: bool = True):
                "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_set_launch",
                "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers", "mrq_debug_race_screen",
                "mrq_set_deadline", "mrq_debug_set_limits", "mrq_probe_peaks",
-               "mrq_set_l2_window", "mrq_read_hamiltonian", "mrq_sci_reference"):
+               "mrq_set_l2_window", "mrq_read_hamiltonian", "mrq_sci_reference", "mrq_load_accumulators"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -325,6 +326,24 @@ class Context:
         ts = np.zeros(NTYPES, np.int64)
         self._check(self._lib.mrq_read_accumulators(self._h, _addr(N), _addr(U), _addr(Wg), _addr(E), _addr(ts)))
         return dict(N=N, U=U, W=Wg, E=E, type_steps=ts)
+
+    def load_accumulators(self, acc, total_steps: int = 0):
+        """Replace the accumulators by given per-group sums (dict with N, U, W, E, type_steps and
+        optionally A, B), e.g. the concatenated groups of several ranks; finalize() then combines them."""
+        N = np.ascontiguousarray(acc["N"], np.float64)
+        G = N.shape[0]
+        U = np.ascontiguousarray(acc["U"], np.float64)
+        Wg = np.ascontiguousarray(acc["W"], np.float64)
+        E = np.ascontiguousarray(acc["E"], np.float64)
+        ts = np.ascontiguousarray(acc["type_steps"], np.int64)
+        A = np.ascontiguousarray(acc["A"], np.float64) if acc.get("A") is not None else None
+        B = np.ascontiguousarray(acc["B"], np.float64) if acc.get("B") is not None else None
+        if U.shape != N.shape or N.shape[1] != self.n_labels or Wg.shape != (G,) or E.shape != (G,) or ts.shape != (NTYPES,):
+            raise ValueError("accumulator shapes do not match the loaded system")
+        self._check(self._lib.mrq_load_accumulators(self._h, G, _addr(N), _addr(U), _addr(Wg), _addr(E),
+                                                    _addr(A) if A is not None else None,
+                                                    _addr(B) if B is not None else None, _addr(ts),
+                                                    int(total_steps)))
 
     def set_launch(self, warps_per_walker=0, steps_per_launch=0, use_graph=False):
         """Walk launch configuration: warps per walker block (0 = chosen from the system's size),

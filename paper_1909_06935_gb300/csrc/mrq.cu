@@ -1898,7 +1898,7 @@ static int finalize_with(mrq_ctx* ctx, mrq_result* out, double* scratch, int nch
 
 int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
     if (!ctx || !out) return MRQ_INVALID_ARG;
-    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    if (!ctx->ref || !ctx->d_accN) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
     CK(cudaSetDevice(ctx->device));
     int nchunk = 0;
     const long long need = fin_scratch_doubles(ctx, &nchunk);
@@ -1913,7 +1913,7 @@ int mrq_finalize(mrq_ctx* ctx, mrq_result* out) {
 int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out) {
     if (!ctx || !out) return MRQ_INVALID_ARG;
     ctx->err[0] = 0;
-    if (!ctx->ref || !ctx->d_walk) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
+    if (!ctx->ref || !ctx->d_accN) return fail(ctx, MRQ_NOT_LOADED, "walkers not initialised");
     double* scratch = nullptr;
     if (ctx->device >= 0 && ctx->device < MRQ_MAX_DEVICES) {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -2274,6 +2274,55 @@ int mrq_read_accumulators(mrq_ctx* ctx, double* accN, double* accU, double* accW
         CK(cudaMemcpyAsync(type_steps, ctx->d_types, sizeof(int64_t) * MRQ_NTYPES, cudaMemcpyDeviceToHost, ctx->stream));
     if (int r_ = sync_stream(ctx)) return r_;
     return 0;
+}
+
+int mrq_load_accumulators(mrq_ctx* ctx, int32_t n_groups, const double* accN, const double* accU, const double* accW,
+                          const double* accE, const double* accA, const double* accB, const int64_t* type_steps,
+                          int64_t total_steps) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ref) return fail(ctx, MRQ_NOT_LOADED, "no reference loaded");
+    if (n_groups <= 0 || n_groups > 64 || !accN || !accU || !accW || !accE || !type_steps || total_steps < 0)
+        return fail(ctx, MRQ_INVALID_ARG, "need 1 <= n_groups <= 64, the N, U, W, E sums and the type counts");
+    CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
+    DeadlinePause pause_(ctx);
+    if (ctx->acc_lab != ctx->nlab || ctx->acc_G != n_groups) {
+        dfree(ctx->d_accN);
+        dfree(ctx->d_accU);
+        dfree(ctx->d_accA);
+        dfree(ctx->d_accB);
+        dfree(ctx->d_accW);
+        dfree(ctx->d_accE);
+        dfree(ctx->d_types);
+        CK(cudaMalloc(&ctx->d_accN, sizeof(double) * ctx->nlab * n_groups));
+        CK(cudaMalloc(&ctx->d_accU, sizeof(double) * ctx->nlab * n_groups));
+        CK(cudaMalloc(&ctx->d_accA, sizeof(double) * ctx->nlab * n_groups));
+        CK(cudaMalloc(&ctx->d_accB, sizeof(double) * ctx->nlab * n_groups));
+        CK(cudaMalloc(&ctx->d_accW, sizeof(double) * n_groups));
+        CK(cudaMalloc(&ctx->d_accE, sizeof(double) * n_groups));
+        CK(cudaMalloc(&ctx->d_types, sizeof(unsigned long long) * MRQ_NTYPES));
+        ctx->acc_lab = ctx->nlab;
+        ctx->acc_G = n_groups;
+    }
+    const long long L = ctx->nlab * n_groups;
+    CK(cudaMemcpyAsync(ctx->d_accN, accN, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_accU, accU, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
+    if (accA) CK(cudaMemcpyAsync(ctx->d_accA, accA, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
+    else CK(cudaMemsetAsync(ctx->d_accA, 0, sizeof(double) * L, ctx->stream));
+    if (accB) CK(cudaMemcpyAsync(ctx->d_accB, accB, sizeof(double) * L, cudaMemcpyDefault, ctx->stream));
+    else CK(cudaMemsetAsync(ctx->d_accB, 0, sizeof(double) * L, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_accW, accW, sizeof(double) * n_groups, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_accE, accE, sizeof(double) * n_groups, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_types, type_steps, sizeof(int64_t) * MRQ_NTYPES, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    ctx->G = n_groups;
+    ctx->nwalk = 0;                    // the walkers no longer match the groups: walkers_init first
+    ctx->total_steps = total_steps;
+    ctx->walk_ms = 0.0;
+    ctx->launches = 0;
+    if (int r = push_sys(ctx)) return r;
+    return sync_stream(ctx);
 }
 
 int mrq_read_gradient_sums(mrq_ctx* ctx, double* accA, double* accB) {

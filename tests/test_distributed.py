@@ -45,3 +45,57 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(bench.argparse.Namespace(steps=1, warmup=0, cpu_seconds=1.0, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def _acc_worker(rank, world, port, out):
+    import numpy as np
+    import torch.distributed as dist
+    import bench
+    import oracle as O
+    from tests.test_oracle import SYSTEMS, tiny
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    s = tiny(**SYSTEMS["1c2a2v"])
+    o = O.Oracle.from_system(s)
+    G = bench.groups_per_rank(world)
+    acc = o.sample(64, 200, 20, seed=500 + rank, n_groups=G)      # each rank its own walkers and seed
+    acc = {k: acc[k] for k in ("N", "U", "W", "E", "A", "B")}
+    acc["type_steps"] = np.zeros(9, np.int64)
+    acc["type_steps"][0] = 64 * 180
+    acc["total_steps"] = 64 * 200
+    objs = [None] * world
+    dist.all_gather_object(objs, acc)
+    merged = bench.merge_rank_accumulators(objs)
+    in_order = all(np.array_equal(merged[k][r * G:(r + 1) * G], objs[r][k])
+                   for k in ("N", "U", "W", "E", "A", "B") for r in range(world))
+    out[rank] = (merged["N"].shape[0], merged["total_steps"], float(o.finalize(merged)["e2"]),
+                 float(o.finalize(merged)["e2_sigma"]),
+                 [float(o.finalize({k: v for k, v in a.items()})["e2"]) for a in objs], in_order,
+                 int(merged["type_steps"][0]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_combine_their_walker_groups():
+    """The cross-rank reduction: every rank's groups gathered, concatenated in rank order and
+    finalized as one run; the union's estimate is the weighted combination of the ranks' (the
+    sums add up) and both ranks see the same union."""
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_acc_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    g0, n0, e0, s0, per0, ord0, t0 = out[0]
+    g1, n1, e1, s1, per1, ord1, t1 = out[1]
+    assert ord0 and ord1 and t0 == t1 == 2 * 64 * 180
+    import bench
+    assert g0 == g1 == 2 * bench.groups_per_rank(2)
+    assert n0 == n1 == 2 * 64 * 200
+    assert e0 == e1 and s0 == s1 and s0 > 0
+    assert per0 == per1 and per0[0] != per0[1]
+    assert abs(e0 - 0.5 * sum(per0)) < 5 * s0
+
+
+def test_groups_per_rank_keeps_the_union_within_64():
+    import bench
+    for w in (1, 2, 3, 4, 5, 8, 16, 64, 100):
+        assert 1 <= bench.groups_per_rank(w) <= 16
+        assert w * bench.groups_per_rank(w) <= 64 or bench.groups_per_rank(w) == 1
