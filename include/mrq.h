@@ -453,6 +453,18 @@ int mrq_load_accumulators(mrq_ctx* ctx, int32_t n_groups, const double* accN, co
                           int64_t total_steps);
 
 /*
+ * Heat-bath cutoff of the walk (Sec. II D generates the excitations by the heat-bath algorithm,
+ * whose cutoff the paper sets to zero: all excitations).  With eps > 0 every double excitation
+ * whose matrix element |<ab||ij>| (|<ab|ij>| for opposite spins) is below eps is dropped wherever
+ * the walk uses one: the walker's neighbours (E_L, rates, moves), the reach-back overlaps O(m),
+ * and the H_D numerator; singles and diagonals stay exact, and E0 is the unscreened <phi0|H|phi0>.
+ * The result is the method applied to that screened Hamiltonian (an approximation; eps = 0
+ * restores the exact method).  Reloading the Hamiltonian resets it to 0.  Errors: MRQ_NOT_LOADED,
+ * MRQ_INVALID_ARG (negative or not finite).
+ */
+int mrq_set_heat_bath_cutoff(mrq_ctx* ctx, double eps);
+
+/*
  * Copy the loaded integrals back (h1: n*n doubles, eri: the 8-fold packed array; either may be
  * NULL), e.g. after mrq_sci_reference rotated them.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
  */

@@ -73,6 +73,8 @@ def _load():
             lib.oracle_philox.argtypes = [P, P, P]
             lib.oracle_walk_one.restype = C.c_int
             lib.oracle_walk_one.argtypes = [P, C.c_uint32, C.c_int64, C.c_uint64, P]
+            lib.oracle_set_hb_eps.argtypes = [P, C.c_double]
+            lib.oracle_set_hb_eps.restype = None
             lib.oracle_set_threads.argtypes = [C.c_int]
             lib.oracle_set_threads.restype = None
             lib.oracle_neighbour_ids.restype = C.c_int64
@@ -139,6 +141,11 @@ class Oracle:
         if h:
             self._lib.oracle_free(h)
             self._h = None
+
+    def set_hb_eps(self, eps: float):
+        """Heat-bath cutoff (Sec. II D): double excitations with |<ab||ij>| < eps are dropped from the
+        walk, the overlaps and the brute force from now on (0: exact).  E0 and the set-up stay exact."""
+        self._lib.oracle_set_hb_eps(self._h, float(eps))
 
     # ---- single determinants
     def _det(self, d):

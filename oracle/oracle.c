@@ -57,6 +57,7 @@ typedef struct {
     double sum_eps_core;
     int64_t start;        /* index (input order) of the largest |phi0| determinant */
     det_t start_det;
+    double hb_eps;        /* heat-bath cutoff of the walk's double excitations (0: exact) */
 } osys;
 
 /* ------------------------------------------------------------------ determinants */
@@ -210,7 +211,10 @@ static double h_elem(const osys *S, const det_t *nd, const det_t *md) {
     int s1 = single_sign(S, &mid, i, a);
     clrb(&mid, i, n); setb(&mid, a, n);
     int s2 = single_sign(S, &mid, j, b);
-    return (double)(s1 * s2) * (phys(S, a, b, i, j) - phys(S, a, b, j, i));
+    double v = (double)(s1 * s2) * (phys(S, a, b, i, j) - phys(S, a, b, j, i));
+    /* heat-bath cutoff (Sec. II D): a double excitation with |<ab||ij>| below it is not generated */
+    if (S->hb_eps > 0.0 && fabs(v) < S->hb_eps) v = 0.0;
+    return v;
 }
 
 /* ------------------------------------------------------------------ Dyall H_D (Sec. II C) */
@@ -344,6 +348,12 @@ static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 void oracle_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox4x32_10(ctr, key, out); }
 
 /* threads of the parallel regions that follow (0 or less: the OpenMP default) */
+/* heat-bath cutoff of the walk (Sec. II D): double excitations with |<ab||ij>| < eps are dropped
+ * from every later neighbour list, overlap and brute-force sum; E0 and the set-up stay exact */
+void oracle_set_hb_eps(void *h, double eps) {
+    ((osys *)h)->hb_eps = eps > 0.0 ? eps : 0.0;
+}
+
 void oracle_set_threads(int n) {
 #ifdef _OPENMP
     if (n > 0) omp_set_num_threads(n);

@@ -155,6 +155,7 @@ def load_library(build_if_missing: bool = True):
     lib.mrq_set_l2_window.argtypes = [P, C.c_double]
     lib.mrq_debug_set_limits.argtypes = [P, C.c_int, C.c_int]
     lib.mrq_read_hamiltonian.argtypes = [P, P, P]
+    lib.mrq_set_heat_bath_cutoff.argtypes = [P, C.c_double]
     lib.mrq_load_accumulators.argtypes = [P, C.c_int32, P, P, P, P, P, P, P, I64]
     lib.mrq_sci_reference.argtypes = [P, C.POINTER(SciParams), C.POINTER(SciResult), P, P]
     for fn in ("mrq_create", "mrq_set_stream", "mrq_load_hamiltonian", "mrq_load_reference", "mrq_set_coeffs",
@@ -163,7 +164,7 @@ def load_library(build_if_missing: bool = True):
                "mrq_amsgrad_step", "mrq_read_coeffs", "mrq_read_gradient_sums", "mrq_sample", "mrq_set_launch",
                "mrq_tune_batch", "mrq_read_accumulators", "mrq_read_walkers", "mrq_debug_race_screen",
                "mrq_set_deadline", "mrq_debug_set_limits", "mrq_probe_peaks",
-               "mrq_set_l2_window", "mrq_read_hamiltonian", "mrq_sci_reference", "mrq_load_accumulators"):
+               "mrq_set_l2_window", "mrq_read_hamiltonian", "mrq_sci_reference", "mrq_load_accumulators", "mrq_set_heat_bath_cutoff"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -411,6 +412,10 @@ class Context:
         self._check(self._lib.mrq_debug_race_screen(self._h, k.size, _addr(k), _addr(r), _addr(tb), _addr(ok),
                                                     _addr(ex)))
         return ok.astype(bool), ex
+
+    def set_heat_bath_cutoff(self, eps: float):
+        """Drop double excitations with |<ab||ij>| < eps from the walk (0: exact)."""
+        self._check(self._lib.mrq_set_heat_bath_cutoff(self._h, float(eps)))
 
     def read_hamiltonian(self):
         """The loaded integrals (h1 as n x n, the packed eri)."""

@@ -483,8 +483,8 @@ __global__ void k_build_tab(const SysDev* __restrict__ sys, double* __restrict__
         const int s = (int)(t % v) + S.nc, r = (int)((t / v) % v) + S.nc;
         const int q = (int)((t / (v * v)) % a), p = (int)(t / (v * v * a));
         const double d = eri_g(S, p, r, q, s), x = eri_g(S, p, s, q, r);
-        tab[t] = d;
-        tab[half + t] = d - x;
+        tab[t] = hb_screen(S, d);                 // every double the CAS path takes reads one entry
+        tab[half + t] = hb_screen(S, d - x);
     }
 }
 
@@ -2425,6 +2425,22 @@ int mrq_read_walkers(mrq_ctx* ctx, uint64_t* dets, double* psi) {
         if (psi) psi[i] = w[i].psi;
     }
     return 0;
+}
+
+int mrq_set_heat_bath_cutoff(mrq_ctx* ctx, double eps) {
+    if (!ctx) return MRQ_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->ham) return fail(ctx, MRQ_NOT_LOADED, "load the Hamiltonian first");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(ctx, MRQ_INVALID_ARG, "the cutoff must be finite and >= 0");
+    CK(cudaSetDevice(ctx->device));
+    if (int r = sync_stream(ctx)) return r;
+    DeadlinePause pause_(ctx);
+    ctx->hsys.hb_eps = eps;
+    ctx->hsys.hb_on = eps > 0.0 ? 1 : 0;
+    if (int r = push_sys(ctx)) return r;
+    k_build_tab<<<2432, 256, 0, ctx->stream>>>(ctx->d_sys, ctx->d_tab);
+    CK(cudaGetLastError());
+    return sync_stream(ctx);
 }
 
 int mrq_read_hamiltonian(mrq_ctx* ctx, double* h1, double* eri) {

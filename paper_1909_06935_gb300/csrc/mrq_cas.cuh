@@ -100,8 +100,8 @@ __device__ __forceinline__ void apply_exc(unsigned long long (&m)[2][W], const S
                                           const int* add, int k) {
     for (int i = 0; i < k; i++) {
         int s1 = rem[i] >= S.n, s2 = add[i] >= S.n;
-        flip<W>(m[s1], rem[i] - s1 * S.n);
-        flip<W>(m[s2], add[i] - s2 * S.n);
+        flip_reg<W>(m, s1, rem[i] - s1 * S.n);
+        flip_reg<W>(m, s2, add[i] - s2 * S.n);
     }
 }
 
@@ -146,17 +146,17 @@ __device__ __forceinline__ double dbl_elem_code(const SysDev& S, const unsigned 
     const int n = S.n;
     const int s_r1 = r1 >= n, s_r2 = r2 >= n;
     const int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - (a1 >= n) * n, pa2 = a2 - (a2 >= n) * n;
-    int c1 = popc_between<W>(m[s_r1], min(pr1, pa1), max(pr1, pa1));
+    int c1 = popc_sel<W>(m, s_r1, min(pr1, pa1), max(pr1, pa1));
     int c2;
     if (s_r2 == s_r1) {
         unsigned long long t[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) t[w] = m[s_r1][w];
+        for (int w = 0; w < W; w++) t[w] = s_r1 ? m[1][w] : m[0][w];
         flip<W>(t, pr1);
         flip<W>(t, pa1);
         c2 = popc_between<W>(t, min(pr2, pa2), max(pr2, pa2));
     } else {
-        c2 = popc_between<W>(m[s_r2], min(pr2, pa2), max(pr2, pa2));
+        c2 = popc_sel<W>(m, s_r2, min(pr2, pa2), max(pr2, pa2));
     }
     double v = __ldg(S.eri4 + eri_idx(S, pa1, pr1, pa2, pr2));
     ctr.g();
@@ -197,17 +197,17 @@ __device__ __forceinline__ void dbl_entry(const SysDev& S, const unsigned long l
     // sign of the reference lane's element (pairing r1 -> a1, r2 -> a2, sequential singles on m)
     const int s_r1 = r1 >= n, s_r2 = r2 >= n;
     const int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - (a1 >= n) * n, pa2 = a2 - (a2 >= n) * n;
-    int c1 = popc_between<W>(mref[s_r1], min(pr1, pa1), max(pr1, pa1));
+    int c1 = popc_sel<W>(mref, s_r1, min(pr1, pa1), max(pr1, pa1));
     int c2;
     if (s_r2 == s_r1) {
         unsigned long long t[W];
 #pragma unroll
-        for (int w2 = 0; w2 < W; w2++) t[w2] = mref[s_r1][w2];
+        for (int w2 = 0; w2 < W; w2++) t[w2] = s_r1 ? mref[1][w2] : mref[0][w2];
         flip<W>(t, pr1);
         flip<W>(t, pa1);
         c2 = popc_between<W>(t, min(pr2, pa2), max(pr2, pa2));
     } else {
-        c2 = popc_between<W>(mref[s_r2], min(pr2, pa2), max(pr2, pa2));
+        c2 = popc_sel<W>(mref, s_r2, min(pr2, pa2), max(pr2, pa2));
     }
     const int sA0 = A0 >= n, sA1 = A1 >= n, sR0 = R0 >= n, sR1 = R1 >= n;
     const bool same = sA0 == sA1 && sR0 == sR1 && sA0 == sR0;
@@ -318,7 +318,7 @@ __device__ __forceinline__ double sgl_elem_code(const SysDev& S, const double* g
     v += single_corr(S, sx, px, py, ad0) - single_corr(S, sx, px, py, rm0);
     if (r == 2) v += single_corr(S, sx, px, py, ad1) - single_corr(S, sx, px, py, rm1);
     ctr.g(1 + 4 * r);
-    return neg_if(v, popc_between<W>(m[sx], min(px, py), max(px, py)));
+    return neg_if(v, popc_sel<W>(m, sx, min(px, py), max(px, py)));
 }
 
 // the cnt (1 or 2) items made of k1 "first" items (f0, f1) and then (s0, s1), sorted when cnt = 2
@@ -354,12 +354,12 @@ __device__ __forceinline__ void group_neighbour(const SysDev& S, const unsigned 
         for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
     {
         int s1 = rm0 >= S.n, s2 = ad0 >= S.n;
-        flip<W>(m[s1], rm0 - s1 * S.n);
-        flip<W>(m[s2], ad0 - s2 * S.n);
+        flip_reg<W>(m, s1, rm0 - s1 * S.n);
+        flip_reg<W>(m, s2, ad0 - s2 * S.n);
     }
     if (r == 2) {
         int s1 = rm1 >= S.n, s2 = ad1 >= S.n;
-        flip<W>(m[s1], rm1 - s1 * S.n);
-        flip<W>(m[s2], ad1 - s2 * S.n);
+        flip_reg<W>(m, s1, rm1 - s1 * S.n);
+        flip_reg<W>(m, s2, ad1 - s2 * S.n);
     }
 }

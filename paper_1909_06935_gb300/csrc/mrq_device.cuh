@@ -70,10 +70,19 @@ struct SysDev {
     int unit_off[9];         // first unit of pair class k = 3 ka + kb (k < 8); unit_off[8] = all units
     int nch[8];              // chunks per (X_a, Y_a) pair of class k
     int gstride;             // doubles of the walker's single-excitation operator, 2 nca nav
-    int pad_;
+    int hb_on;               // heat-bath cutoff in force (hb_eps > 0)
     const unsigned short* colex;       // pair decode table: colex[j(j-1)/2 + i] = i | j << 8, i < j < 128
     unsigned long long mag_c, mag_v;   // ceil(2^64 / n_core), ceil(2^64 / n_virt) (0 when that is <= 1)
+    double hb_eps;           // heat-bath cutoff: double excitations with |<ab||ij>| < hb_eps are dropped
 };
+
+// The heat-bath cutoff (Sec. II D generates excitations by the heat-bath algorithm; with a
+// positive cutoff it drops every double excitation whose element |<ab||ij>| is below it): the walk's
+// double-excitation elements pass through this screen.  Off (no FP64 compare) at cutoff zero.
+__device__ __forceinline__ double hb_screen(const SysDev& S, double v) {
+    if (S.hb_on && fabs(v) < S.hb_eps) v = 0.0;
+    return v;
+}
 
 // ------------------------------------------------------------------ access counters
 // The walk uses NoCtr (compiles away); the parity/debug kernel uses Ctr to report, per
@@ -151,13 +160,44 @@ __device__ __forceinline__ int sgn_single(const unsigned long long* s, int p, in
     return (popc_between<W>(s, lo, hi) & 1) ? -1 : 1;
 }
 
+// popc_between / sgn_single on spin string sg of a determinant (row chosen by selects)
+template <int W>
+__device__ __forceinline__ int popc_sel(const unsigned long long (&d)[2][W], int sg, int lo, int hi) {
+    unsigned long long r[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) r[w] = sg ? d[1][w] : d[0][w];
+    return popc_between<W>(r, lo, hi);
+}
+
+template <int W>
+__device__ __forceinline__ int sgn_sel(const unsigned long long (&d)[2][W], int sg, int p, int q) {
+    return (popc_sel<W>(d, sg, p < q ? p : q, p < q ? q : p) & 1) ? -1 : 1;
+}
+
 template <int W>
 __device__ __forceinline__ bool bit_of(const unsigned long long* s, int p) {
     return (s[p >> 6] >> (p & 63)) & 1ull;
 }
 template <int W>
 __device__ __forceinline__ void flip(unsigned long long* s, int p) {
-    s[p >> 6] ^= (1ull << (p & 63));
+    const unsigned long long b = 1ull << (p & 63);
+    if (W == 1) {
+        s[0] ^= b;
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; w++) s[w] ^= (p >> 6) == w ? b : 0ull;   // word chosen by selects, not an index
+    }
+}
+
+// the same on spin string sg of a determinant, with every array index known at compile time so
+// that the determinant stays in registers (a runtime row index would put it in local memory)
+template <int W>
+__device__ __forceinline__ void flip_reg(unsigned long long (&m)[2][W], int sg, int p) {
+    const unsigned long long b = 1ull << (p & 63);
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int w = 0; w < W; w++) m[s][w] ^= (s == sg && (W == 1 || (p >> 6) == w)) ? b : 0ull;
 }
 
 // active bits of a spin string, right-aligned (n_act <= 32; the active block may straddle a word)
@@ -280,7 +320,7 @@ __device__ double single_elem(const SysDev& S, const unsigned long long (&d)[2][
             if (sg == sx) { v += eri_g(S, py, j, j, px); ctr.g(); }
         }
     }
-    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_between<W>(d[sx], px < py ? px : py, px < py ? py : px) & 1) << 63));
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_sel<W>(d, sx, px < py ? px : py, px < py ? py : px) & 1) << 63));
 }
 
 // <d'|H|d> for the double r1,r2 -> a1,a2 (spin orbitals, r1<r2, a1<a2, spin conserving)
@@ -291,17 +331,17 @@ __device__ __forceinline__ double double_elem(const SysDev& S, const unsigned lo
     int s_r1 = r1 >= n, s_r2 = r2 >= n, s_a1 = a1 >= n, s_a2 = a2 >= n;
     int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - s_a1 * n, pa2 = a2 - s_a2 * n;
     // pairing r1->a1, r2->a2 (spin conserving by the ordering of spin orbitals)
-    int c1 = popc_between<W>(d[s_r1], pr1 < pa1 ? pr1 : pa1, pr1 < pa1 ? pa1 : pr1);
+    int c1 = popc_sel<W>(d, s_r1, pr1 < pa1 ? pr1 : pa1, pr1 < pa1 ? pa1 : pr1);
     int c2;
     if (s_r2 == s_r1) {
         unsigned long long t[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) t[w] = d[s_r1][w];
+        for (int w = 0; w < W; w++) t[w] = s_r1 ? d[1][w] : d[0][w];
         flip<W>(t, pr1);
         flip<W>(t, pa1);
         c2 = popc_between<W>(t, pr2 < pa2 ? pr2 : pa2, pr2 < pa2 ? pa2 : pr2);
     } else {
-        c2 = popc_between<W>(d[s_r2], pr2 < pa2 ? pr2 : pa2, pr2 < pa2 ? pa2 : pr2);
+        c2 = popc_sel<W>(d, s_r2, pr2 < pa2 ? pr2 : pa2, pr2 < pa2 ? pa2 : pr2);
     }
     double v = eri_g(S, pa1, pr1, pa2, pr2);
     ctr.g();
@@ -329,7 +369,7 @@ __device__ double hd_single_elem(const SysDev& S, const unsigned long long (&d)[
                 if (sg == sx) { v -= eri_g(S, py, j, j, px); ctr.g(); }
             }
         }
-    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_between<W>(d[sx], px < py ? px : py, px < py ? py : px) & 1) << 63));
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_sel<W>(d, sx, px < py ? px : py, px < py ? py : px) & 1) << 63));
 }
 
 // ------------------------------------------------------------------ reach-back (Eq. 6-7)
@@ -492,7 +532,7 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                         ctr.term();
                         int r1 = R[0] < R[1] ? R[0] : R[1], r2 = R[0] < R[1] ? R[1] : R[0];
                         int a1 = A[0] < A[1] ? A[0] : A[1], a2 = A[0] < A[1] ? A[1] : A[0];
-                        acc += double_elem<W>(S, m, r1, r2, a1, a2, ctr) * c;
+                        acc += hb_screen(S, double_elem<W>(S, m, r1, r2, a1, a2, ctr)) * c;
                     }
                 }
             }

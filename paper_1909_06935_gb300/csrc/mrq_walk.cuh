@@ -28,8 +28,12 @@
 #define MRQ_CAS_CH 128        // neighbours per unit inside the CAS
 #define MRQ_FOIS_CH 128       // neighbours per unit of a FOIS walker
 #define MRQ_UNIT_NB 1024      // neighbours per unit of an (X_a, Y_a) pair (pairs are cut into chunks)
+// walk blocks of MRQ_MAXNW warps resident per SM (bounds the registers): one-word determinants
+// (n <= 64) fit three blocks' shared memory per SM, and three blocks at 80 registers beat two at
+// 128 (250 vs 263 ms per step at 56 orbitals); two-word systems keep 128 registers, since their
+// candidate lists and operator leave shared memory for two blocks only
 #ifndef MRQ_WALK_MINB
-#define MRQ_WALK_MINB 2       // walk blocks of MRQ_MAXNW warps resident per SM (bounds the registers)
+#define MRQ_WALK_MINB(W) ((W) == 1 ? 3 : 2)
 #endif
 
 // the walker block's shared state (dynamic shared memory starts with it)
@@ -298,17 +302,17 @@ __device__ __forceinline__ double double_elem_tab(const SysDev& S, const unsigne
     const int n = S.n;
     const int s_r1 = r1 >= n, s_r2 = r2 >= n;
     const int pr1 = r1 - s_r1 * n, pr2 = r2 - s_r2 * n, pa1 = a1 - (a1 >= n) * n, pa2 = a2 - (a2 >= n) * n;
-    int c1 = popc_between<W>(d[s_r1], min(pr1, pa1), max(pr1, pa1));
+    int c1 = popc_sel<W>(d, s_r1, min(pr1, pa1), max(pr1, pa1));
     int c2;
     if (s_r2 == s_r1) {
         unsigned long long t[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) t[w] = d[s_r1][w];
+        for (int w = 0; w < W; w++) t[w] = s_r1 ? d[1][w] : d[0][w];
         flip<W>(t, pr1);
         flip<W>(t, pa1);
         c2 = popc_between<W>(t, min(pr2, pa2), max(pr2, pa2));
     } else {
-        c2 = popc_between<W>(d[s_r2], min(pr2, pa2), max(pr2, pa2));
+        c2 = popc_sel<W>(d, s_r2, min(pr2, pa2), max(pr2, pa2));
     }
     const unsigned sv = (unsigned)S.nav, sq = sv * sv, sp = sq * (unsigned)S.nca;
     const unsigned idx = (s_r1 == s_r2 ? S.tab_half : 0u) + (unsigned)pr1 * sp + (unsigned)pr2 * sq +
@@ -495,7 +499,7 @@ __device__ void cas_pair_unit(const SysDev& S, const CasWalker& cw, const double
                                 // single n -> m (x = rm0 -> y = ad0): the walker's operator G
                                 const int sx = rm0 >= S.n, px = rm0 - sx * S.n, py = ad0 - sx * S.n;
                                 hnm = neg_if(gops[(sx * S.nca + px) * S.nav + (py - S.nc)],
-                                             sgn_single<W>(n[sx], px, py) < 0 ? 1 : 0);
+                                             sgn_sel<W>(n, sx, px, py) < 0 ? 1 : 0);
                                 ctr.g();
                             } else {
                                 hnm = double_elem_tab<W>(S, n, rm0, rm1, ad0, ad1, ctr);
@@ -586,16 +590,16 @@ __device__ __noinline__ void fois_unit(const SysDev& S, const WarpSh& sh, const 
             for (int w = 0; w < W; w++) m[sg][w] = n[sg][w];
         {
             int s1 = r1 >= S.n, s2 = a1 >= S.n;
-            flip<W>(m[s1], r1 - s1 * S.n);
-            flip<W>(m[s2], a1 - s2 * S.n);
+            flip_reg<W>(m, s1, r1 - s1 * S.n);
+            flip_reg<W>(m, s2, a1 - s2 * S.n);
             if (kind != 0) {
                 int s3 = r2 >= S.n, s4 = a2 >= S.n;
-                flip<W>(m[s3], r2 - s3 * S.n);
-                flip<W>(m[s4], a2 - s4 * S.n);
+                flip_reg<W>(m, s3, r2 - s3 * S.n);
+                flip_reg<W>(m, s4, a2 - s4 * S.n);
             }
         }
         const double hnm =
-            (kind == 0) ? single_elem<W>(S, n, r1, a1, ctr) : double_elem<W>(S, n, r1, r2, a1, a2, ctr);
+            (kind == 0) ? single_elem<W>(S, n, r1, a1, ctr) : hb_screen(S, double_elem<W>(S, n, r1, r2, a1, a2, ctr));
         int hm, pm;
         const long long lm = det_label<W>(S, m, hm, pm);
         double om, psim;
@@ -816,21 +820,21 @@ template <int W>
 __device__ __forceinline__ void apply_code(unsigned long long (&m)[2][W], const SysDev& S, unsigned exc) {
     const int r1 = exc & 255u, r2 = (exc >> 8) & 255u, a1 = (exc >> 16) & 255u, a2 = (exc >> 24) & 255u;
     int s = r1 >= S.n;
-    flip<W>(m[s], r1 - s * S.n);
+    flip_reg<W>(m, s, r1 - s * S.n);
     s = a1 >= S.n;
-    flip<W>(m[s], a1 - s * S.n);
+    flip_reg<W>(m, s, a1 - s * S.n);
     if (r2 != r1) {
         s = r2 >= S.n;
-        flip<W>(m[s], r2 - s * S.n);
+        flip_reg<W>(m, s, r2 - s * S.n);
         s = a2 >= S.n;
-        flip<W>(m[s], a2 - s * S.n);
+        flip_reg<W>(m, s, a2 - s * S.n);
     }
 }
 
 // One walker step per block: slot blockIdx.x (or order[blockIdx.x]) of the walk set.  The step's
 // contribution goes into the walker's record; k_accum adds the records into the accumulators.
 template <int W>
-__global__ void __launch_bounds__(MRQ_MAXNW * 32, MRQ_WALK_MINB) k_walk2(const WalkSet ws, const unsigned* __restrict__ order,
+__global__ void __launch_bounds__(MRQ_MAXNW * 32, MRQ_WALK_MINB(W)) k_walk2(const WalkSet ws, const unsigned* __restrict__ order,
                                                              int accumulate) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     CtaSh& cs = *reinterpret_cast<CtaSh*>(smem_dyn);
