@@ -1068,6 +1068,7 @@ struct mrq_ctx {
     int probe_limit = 0, cap_limit = 0;
     int cand_cap_full = 1;           // the candidate-list capacity the loaded system needs
     double l2_fraction = 0.0;        // mrq_set_l2_window: share of the persisting-L2 carve-out for the tables
+    int walk_minb = 2;               // resident walk blocks per SM of the kernel build in use (2, 3, 4)
 };
 
 static int fail(mrq_ctx* c, int code, const char* fmt, ...) {
@@ -1222,9 +1223,27 @@ static int walk_sort_prepare(mrq_ctx* ctx, long long nslots, long long max_seg) 
     return 0;
 }
 
-static int walk_attr_prepare(mrq_ctx* ctx, int W, size_t smem) {
-    if (W == 1) CK(cudaFuncSetAttribute(k_walk2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else CK(cudaFuncSetAttribute(k_walk2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <int W, int B>
+static int walk_fits(mrq_ctx* ctx, size_t smem, int threads, bool& fits) {
+    CK(cudaFuncSetAttribute(k_walk2<W, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk2<W, B>, threads, smem));
+    fits = nb >= B;
+    return 0;
+}
+
+// the walk kernel's build for this launch: the most resident blocks per SM (4, 3 or 2, fewer
+// registers each) that the block's shared memory allows
+static int walk_attr_prepare(mrq_ctx* ctx, int W, size_t smem, int threads) {
+    bool f4 = false, f3 = false, f2 = false;
+    if (W == 1) {
+        if (int r = walk_fits<1, 4>(ctx, smem, threads, f4)) return r;
+        if (int r = walk_fits<1, 3>(ctx, smem, threads, f3)) return r;
+        if (int r = walk_fits<1, 2>(ctx, smem, threads, f2)) return r;
+    } else {
+        if (int r = walk_fits<2, 2>(ctx, smem, threads, f2)) return r;
+    }
+    ctx->walk_minb = f4 ? 4 : (f3 ? 3 : 2);
     return 0;
 }
 
@@ -1248,7 +1267,7 @@ static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int c
     const long long nslots = ws.nslots;
     if (!L.captured) {
         if (int r = walk_sort_prepare(ctx, nslots, ws.max_seg)) return r;
-        if (int r = walk_attr_prepare(ctx, W, smem)) return r;
+        if (int r = walk_attr_prepare(ctx, W, smem, 32 * nw)) return r;
     }
     for (int step = 0; step < nsteps; step++) {
         // order every system's slots by determinant (walkers on one determinant in neighbouring blocks)
@@ -1271,8 +1290,10 @@ static int launch_walk(mrq_ctx* ctx, int W, const WalkSet& ws, int nsteps, int c
             cfg.attrs = attr;
             cfg.numAttrs = 1;
         }
-        if (W == 1) CK(cudaLaunchKernelEx(&cfg, k_walk2<1>, ws, order, L.accumulate));
-        else CK(cudaLaunchKernelEx(&cfg, k_walk2<2>, ws, order, L.accumulate));
+        if (W == 2) CK(cudaLaunchKernelEx(&cfg, k_walk2<2, 2>, ws, order, L.accumulate));
+        else if (ctx->walk_minb == 4) CK(cudaLaunchKernelEx(&cfg, k_walk2<1, 4>, ws, order, L.accumulate));
+        else if (ctx->walk_minb == 3) CK(cudaLaunchKernelEx(&cfg, k_walk2<1, 3>, ws, order, L.accumulate));
+        else CK(cudaLaunchKernelEx(&cfg, k_walk2<1, 2>, ws, order, L.accumulate));
         if (L.accumulate) {
             k_accum<<<dim3((unsigned)ws.nsys, 2), 1024, 0, ctx->stream>>>(ws);
             CK(cudaGetLastError());
@@ -2045,7 +2066,9 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstrid
     const int64_t nfull = n_steps / spl, rem = n_steps % spl;
     if (graph && nfull > 0) {
         if (int r = walk_sort_prepare(ctx, ws.nslots, ws.max_seg)) return r;
-        if (int r = walk_attr_prepare(ctx, W, cta_smem_bytes(std::min(wpb, MRQ_MAXNW), cap, gstride))) return r;
+        if (int r = walk_attr_prepare(ctx, W, cta_smem_bytes(std::min(wpb, MRQ_MAXNW), cap, gstride),
+                                      32 * std::min(wpb, MRQ_MAXNW)))
+            return r;
         mrq_ctx::GraphKey key;
         key.sys = ws.systems;
         key.wptr = ws.walkers;

@@ -28,13 +28,10 @@
 #define MRQ_CAS_CH 128        // neighbours per unit inside the CAS
 #define MRQ_FOIS_CH 128       // neighbours per unit of a FOIS walker
 #define MRQ_UNIT_NB 1024      // neighbours per unit of an (X_a, Y_a) pair (pairs are cut into chunks)
-// walk blocks of MRQ_MAXNW warps resident per SM (bounds the registers): one-word determinants
-// (n <= 64) fit three blocks' shared memory per SM, and three blocks at 80 registers beat two at
-// 128 (250 vs 263 ms per step at 56 orbitals); two-word systems keep 128 registers, since their
-// candidate lists and operator leave shared memory for two blocks only
-#ifndef MRQ_WALK_MINB
-#define MRQ_WALK_MINB(W) ((W) == 1 ? 3 : 2)
-#endif
+// The walk kernel is compiled for 2, 3 and 4 resident blocks of MRQ_MAXNW warps per SM (128, 80
+// and 64 registers); the runtime takes the most blocks the launch's shared memory allows.  More
+// resident warps hide more of the gathers' latency: at 56 orbitals (39 KB per block) four blocks
+// beat three and three beat two (239, 245 and 263 ms per step).
 
 // the walker block's shared state (dynamic shared memory starts with it)
 struct CtaSh {
@@ -833,8 +830,8 @@ __device__ __forceinline__ void apply_code(unsigned long long (&m)[2][W], const 
 
 // One walker step per block: slot blockIdx.x (or order[blockIdx.x]) of the walk set.  The step's
 // contribution goes into the walker's record; k_accum adds the records into the accumulators.
-template <int W>
-__global__ void __launch_bounds__(MRQ_MAXNW * 32, MRQ_WALK_MINB(W)) k_walk2(const WalkSet ws, const unsigned* __restrict__ order,
+template <int W, int MINB>
+__global__ void __launch_bounds__(MRQ_MAXNW * 32, MINB) k_walk2(const WalkSet ws, const unsigned* __restrict__ order,
                                                              int accumulate) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     CtaSh& cs = *reinterpret_cast<CtaSh*>(smem_dyn);
