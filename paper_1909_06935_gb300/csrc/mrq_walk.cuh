@@ -34,6 +34,13 @@
 // beat three and three beat two (239, 245 and 263 ms per step).
 
 // the walker block's shared state (dynamic shared memory starts with it)
+struct CasWalker {
+    unsigned long long AOn, AEn, keyn;
+    int cntO, cntE;
+    double phin, c0, inv_psin;
+    float inv_psin_f;
+};
+
 struct CtaSh {
     WarpSh L;                       // the walker's system (L.sys) and occupied / empty lists
     double wsum[3][MRQ_VW];         // per virtual warp sum |t|, sum t, sum t_D
@@ -45,7 +52,22 @@ struct CtaSh {
     long long nbase_fois;
     int units;
     int pad_;
+    // per-thread race state (best exact clock, its psi_s, FP32 image and excitation): kept in shared
+    // memory rather than registers, since it changes only when a candidate beats the lane's best
+    double rbt[MRQ_MAXNW * 32];
+    double rbpsi[MRQ_MAXNW * 32];
+    float rbtf[MRQ_MAXNW * 32];
+    unsigned rbexc[MRQ_MAXNW * 32];
+    // the walker's determinant and CAS constants, read by the work units from shared memory (the
+    // same for every thread; registers stay free for the neighbour loops)
+    CasWalker cw;
+    unsigned long long nsh[4];
 };
+
+__device__ __forceinline__ CtaSh& cta_sh() {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    return *reinterpret_cast<CtaSh*>(smem_dyn);
+}
 
 __host__ __device__ __forceinline__ size_t cta_list_bytes(int cap) {
     return ((size_t)cap * sizeof(double) + (size_t)cap * sizeof(unsigned) + 15) / 16 * 16;
@@ -71,21 +93,19 @@ struct PhCtr : NoCtr {
 };
 #endif
 
-// per-lane running sums of a walker's step (scaled by 1/psi_s(n) once at the end)
+// per-lane running sums of a walker's step (scaled by 1/psi_s(n) once at the end); the lane's race
+// state is in shared memory (CtaSh::rbt ...)
 struct LaneAcc2 {
     double sA, sT, sD;     // sum |t|, sum t, sum t_D   (t = H_nm psi_s(m), t_D = (H_D)_nm psi_s(m))
-    double bt;             // best exact clock
-    float btf;             // its FP32 image
-    unsigned bexc;
-    double bpsi;
 };
 
 __device__ __forceinline__ void acc2_init(LaneAcc2& a) {
     a.sA = a.sT = a.sD = 0.0;
-    a.bt = INFINITY;
-    a.btf = INFINITY;
-    a.bexc = 0xFFFFFFFFu;
-    a.bpsi = 0.0;
+    CtaSh& cs = cta_sh();
+    cs.rbt[threadIdx.x] = INFINITY;
+    cs.rbtf[threadIdx.x] = INFINITY;
+    cs.rbexc[threadIdx.x] = 0xFFFFFFFFu;
+    cs.rbpsi[threadIdx.x] = 0.0;
 }
 
 // the exact FP64 clock, kept out of the hot loop's code (few candidates pass the screen)
@@ -102,15 +122,18 @@ __device__ __forceinline__ void lane_post2(const SysDev& S, LaneAcc2& a, double 
     if (MODE == MODE_STEP) {
         if ((__double_as_longlong(t) << 1) != 0) {          // t != 0, without an FP64 compare
             const unsigned long long k53 = race_bits(S.seed, exc, step, wid);
-            if (race_may_win(k53, abs_f32_of(t) * inv_psin_f, a.btf)) {
+            CtaSh& cs = cta_sh();
+            const int me = threadIdx.x;
+            if (race_may_win(k53, abs_f32_of(t) * inv_psin_f, cs.rbtf[me])) {
                 const double g = fabs(t * inv_psin);
                 if (g > 0.0) {
                     const double tc = race_clock_cold(k53, g);
-                    if (tc < a.bt || (tc == a.bt && exc < a.bexc)) {
-                        a.bt = tc;
-                        a.btf = (float)tc;
-                        a.bexc = exc;
-                        a.bpsi = psim;
+                    const double bt = cs.rbt[me];
+                    if (tc < bt || (tc == bt && exc < cs.rbexc[me])) {
+                        cs.rbt[me] = tc;
+                        cs.rbtf[me] = (float)tc;
+                        cs.rbexc[me] = exc;
+                        cs.rbpsi[me] = psim;
                     }
                 }
             }
@@ -151,12 +174,6 @@ __device__ __forceinline__ unsigned exc_code(int r1, int r2, int a1, int a2) {
 
 // ------------------------------------------------------------------ per-walker constants (CAS)
 
-struct CasWalker {
-    unsigned long long AOn, AEn, keyn;
-    int cntO, cntE;
-    double phin, c0, inv_psin;
-    float inv_psin_f;
-};
 
 // spin-resolved candidate blocks: R' (ne electrons of m's active occupation) and A' (nf holes),
 // alpha(R') - alpha(A') = dsp; block b takes alpha(R') = ib[b]; its index is decoded by multiplying
@@ -356,8 +373,8 @@ __device__ __forceinline__ int cas_unit_count(const SysDev& S, const CasWalker& 
 // neighbours inside the CAS: spin-resolved blocks (alpha singles, beta singles, alpha-alpha,
 // beta-beta, alpha-beta doubles) of the walker's active electrons / holes
 template <int W, int MODE, class C>
-__device__ __noinline__ void cas_internal_unit(const SysDev& S, const CasWalker& cw, const unsigned long long (&n)[2][W], int u,
-                                  LaneAcc2& acc, unsigned step, unsigned wid, int lane, mrq_neighbour* nbout,
+__device__ __noinline__ LaneAcc2 cas_internal_unit(const SysDev& S, const CasWalker& cw, const unsigned long long (&n)[2][W], int u,
+                                  LaneAcc2 acc, unsigned step, unsigned wid, int lane, mrq_neighbour* nbout,
                                   long long nbase, long long max_nb, C& ctr) {
     const unsigned long long oa = cw.AOn & 0xFFFFFFFFull, ob = cw.AOn & ~0xFFFFFFFFull;
     const unsigned long long ea = cw.AEn & 0xFFFFFFFFull, eb = cw.AEn & ~0xFFFFFFFFull;
@@ -422,6 +439,7 @@ __device__ __noinline__ void cas_internal_unit(const SysDev& S, const CasWalker&
             write_rec(nbout + nbase + (idx - i0), w4, W, hnm, 0.0, om, psim, fabs(t * cw.inv_psin), exc);
         }
     }
+    return acc;
 }
 
 // one (X_a, Y_a) pair chunk [lo, hi) of a CAS walker
@@ -566,9 +584,9 @@ __device__ void cas_pair_unit(const SysDev& S, const CasWalker& cw, const double
 
 // neighbours [i0, i1) of the class-block enumeration, reach-back per lane
 template <int W, int MODE, class C>
-__device__ __noinline__ void fois_unit(const SysDev& S, const WarpSh& sh, const unsigned long long (&n)[2][W], long long ln,
+__device__ __noinline__ LaneAcc2 fois_unit(const SysDev& S, const WarpSh& sh, const unsigned long long (&n)[2][W], long long ln,
                           double c0, double inv_psin, float inv_psin_f, unsigned long long self_key, double phi_self,
-                          int i0, int i1, LaneAcc2& acc, unsigned step, unsigned wid, int lane, mrq_neighbour* nbout,
+                          int i0, int i1, LaneAcc2 acc, unsigned step, unsigned wid, int lane, mrq_neighbour* nbout,
                           long long nbase, long long max_nb, C& ctr) {
     for (int idx = i0 + lane; idx < i1; idx += 32) {
         int lo = 0, hi = sh.nb - 1;          // block of idx: last b with bstart[b] <= idx
@@ -620,6 +638,7 @@ __device__ __noinline__ void fois_unit(const SysDev& S, const WarpSh& sh, const 
             write_rec(nbout + nbase + idx, w4, W, hnm, hd, om, psim, fabs(t * inv_psin), exc);
         }
     }
+    return acc;
 }
 
 // ------------------------------------------------------------------ one walker step per block
@@ -699,7 +718,15 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
             gops[t] = v;
         }
         units = S.unit_off[8];
+        if (threadIdx.x == 0) cs.cw = cw;
     }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int sg = 0; sg < 2; sg++)
+#pragma unroll
+            for (int w = 0; w < W; w++) cs.nsh[sg * W + w] = n[sg][w];
+    }
+    const unsigned long long(&nsh)[2][W] = *reinterpret_cast<const unsigned long long(*)[2][W]>(cs.nsh);
     __syncthreads();
     ctr.mark(0);
     const int total_fois = cas ? 0 : cs.L.bstart[cs.L.nb];
@@ -732,17 +759,17 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
             if (cas) {
                 const long long nbase = (MODE == MODE_DEBUG && nbout != nullptr) ? nb_prefix[u] : 0;
                 if (u < S.cas_units) {
-                    cas_internal_unit<W, MODE>(S, cw, n, u, acc, step, wid, lane, nbout, nbase, max_nb, ctr);
+                    acc = cas_internal_unit<W, MODE>(S, cs.cw, nsh, u, acc, step, wid, lane, nbout, nbase, max_nb, ctr);
                     ctr.mark(1);
                 } else {
-                    cas_pair_unit<W, MODE>(S, cw, gops, cphi, ccode, n, u, acc, step, wid, lane, nbout, nbase, max_nb,
-                                           ctr);
+                    cas_pair_unit<W, MODE>(S, cs.cw, gops, cphi, ccode, nsh, u, acc, step, wid, lane, nbout, nbase,
+                                           max_nb, ctr);
                     ctr.mark(2);
                 }
             } else {
                 const int i0 = u * MRQ_FOIS_CH, i1 = min(total_fois, i0 + MRQ_FOIS_CH);
-                fois_unit<W, MODE>(S, cs.L, n, ln, c0, inv_psin, inv_psin_f, self_key, phi_self, i0, i1, acc, step,
-                                   wid, lane, nbout, 0, max_nb, ctr);
+                acc = fois_unit<W, MODE>(S, cs.L, nsh, ln, c0, inv_psin, inv_psin_f, self_key, phi_self, i0, i1, acc,
+                                         step, wid, lane, nbout, 0, max_nb, ctr);
                 ctr.mark(7);
             }
         }
@@ -755,8 +782,10 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
     }
     // the race's winner: smallest clock, then smallest excitation id (order-independent)
     {
-        double t = acc.bt;
-        unsigned e = acc.bexc;
+        const double bt_me = cs.rbt[threadIdx.x];
+        const unsigned be_me = cs.rbexc[threadIdx.x];
+        double t = bt_me;
+        unsigned e = be_me;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const double t2 = __shfl_xor_sync(0xffffffffu, t, o);
@@ -766,9 +795,9 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
                 e = e2;
             }
         }
-        const unsigned win = __ballot_sync(0xffffffffu, acc.bexc == e && acc.bt == t);
+        const unsigned win = __ballot_sync(0xffffffffu, be_me == e && bt_me == t);
         const int src = win ? __ffs(win) - 1 : 0;
-        const double bpsi = __shfl_sync(0xffffffffu, acc.bpsi, src);
+        const double bpsi = cs.rbpsi[(threadIdx.x & ~31u) + src];
         if (lane == 0) {
             cs.wbt[wi] = t;
             cs.wbexc[wi] = e;
