@@ -240,9 +240,11 @@ __device__ __forceinline__ void cand_decode(const SysDev& S, const CandPlan& P, 
 }
 
 // build the candidate list of group (c, v, sc, sv) of active remnant (AOm, AEm): singles [0, n1) as
-// codes, doubles [n1, count) as (signed weight, table base); the candidate k = n is left out
+// codes, doubles [n1, count) as (signed weight, table base); the candidate k = n is left out.  Kept
+// out of line: it runs once per group, and its registers and code then stay out of the neighbour
+// loop that follows (1.8 % faster at 56 orbitals)
 template <int W, class C>
-__device__ __forceinline__ int build_group_list(const SysDev& S, const CasWalker& cw,
+__device__ __noinline__ int build_group_list(const SysDev& S, const CasWalker& cw,
                                                 const unsigned long long (&mref)[2][W], unsigned long long AOm,
                                                 unsigned long long AEm, int c, int v, int sc, int sv, int rxc0,
                                                 int rxc1, int ryv0, int ryv1, int par_ref, double* cphi,
