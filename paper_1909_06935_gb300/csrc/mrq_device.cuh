@@ -380,9 +380,43 @@ __device__ double hd_single_elem(const SysDev& S, const unsigned long long (&d)[
 
 // `self_key`/`self_term`: when the walker n is itself a CAS determinant, the candidate k = n
 // needs no lookup: its term is H_nm phi0(n), both already known (pass self_key = ~0 otherwise).
+// Single elements from a walker's operator: <k|H|m> for the single x -> y of m (x in active +
+// virtual, y in core + active, not both active) is G_yx(m) = h_yx + sum_{j in m} [(yx|jj) - delta
+// (yj|jx)], taken as the walker n's G_yx(n) (g, in shared memory) plus the terms of the <= 4 spin
+// orbitals in which m differs from n (removed rm*, added ad*; r of each), with m's sign.
+struct SglFromWalker {
+    const double* g;        // nullptr: full Slater-Condon sums
+    int r, rm0, rm1, ad0, ad1;   // r = 0: m is the walker itself
+};
+
+// whether the single x -> y lies in the block the walker's operator holds
+__device__ __forceinline__ bool in_walker_block(const SysDev& S, int x, int y) {
+    const int sx = x >= S.n, px = x - sx * S.n, py = y - sx * S.n;
+    return px >= S.nc && py < S.nca && !(py >= S.nc && px < S.nca);
+}
+
+__device__ __forceinline__ double g_corr(const SysDev& S, int sx, int px, int py, int j) {
+    const int sj = j >= S.n, pj = j - sj * S.n;
+    double v = eri_g(S, py, px, pj, pj);
+    if (sj == sx) v -= eri_g(S, py, pj, pj, px);
+    return v;
+}
+
+template <int W, class C>
+__device__ __forceinline__ double single_from_walker(const SysDev& S, const SglFromWalker& G,
+                                                     const unsigned long long (&m)[2][W], int x, int y, C& ctr) {
+    const int sx = x >= S.n, px = x - sx * S.n, py = y - sx * S.n;
+    double v = G.g[(sx * S.nca + py) * S.nav + (px - S.nc)];
+    if (G.r >= 1) v += g_corr(S, sx, px, py, G.ad0) - g_corr(S, sx, px, py, G.rm0);
+    if (G.r == 2) v += g_corr(S, sx, px, py, G.ad1) - g_corr(S, sx, px, py, G.rm1);
+    ctr.g(1 + 4 * G.r);
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(popc_sel<W>(m, sx, px < py ? px : py, px < py ? py : px) & 1) << 63));
+}
+
 template <int W, class C = NoCtr>
 __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W], C& ctr,
-                             unsigned long long self_key = MRQ_EMPTY_KEY, double self_term = 0.0) {
+                             unsigned long long self_key = MRQ_EMPTY_KEY, double self_term = 0.0,
+                             const SglFromWalker& G = SglFromWalker{nullptr, 0, 0, 0, 0, 0}) {
     const int n = S.n, nc = S.nc, na = S.na;
     int hs[2], ps[2], hc = 0, pc = 0;
 #pragma unroll
@@ -454,8 +488,8 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                     continue;
                 }
                 double c = hash_lookup(S, key, ctr);
-                if (c != 0.0) {
-                    acc += single_elem<W>(S, m, x, y, ctr) * c;
+                if ((__double_as_longlong(c) << 1) != 0) {          // c != 0 without an FP64 compare
+                    acc += (G.g ? single_from_walker<W>(S, G, m, x, y, ctr) : single_elem<W>(S, m, x, y, ctr)) * c;
                     ctr.term();
                 }
             }
@@ -528,7 +562,7 @@ __device__ double reach_back(const SysDev& S, const unsigned long long (&m)[2][W
                             continue;
                         }
                         double c = hash_lookup(S, key, ctr);
-                        if (c == 0.0) continue;
+                        if ((__double_as_longlong(c) << 1) == 0) continue;
                         ctr.term();
                         int r1 = R[0] < R[1] ? R[0] : R[1], r2 = R[0] < R[1] ? R[1] : R[0];
                         int a1 = A[0] < A[1] ? A[0] : A[1], a2 = A[0] < A[1] ? A[1] : A[0];

@@ -274,7 +274,7 @@ __device__ __noinline__ int build_group_list(const SysDev& S, const CasWalker& c
                 if (key == cw.keyn) valid = false;
                 else {
                     phi = hash_lookup(S, key, ctr);
-                    valid = phi != 0.0;
+                    valid = (__double_as_longlong(phi) << 1) != 0;      // phi != 0 without an FP64 compare
                 }
             }
             const unsigned vm = __ballot_sync(0xffffffffu, valid);
@@ -586,7 +586,8 @@ __device__ void cas_pair_unit(const SysDev& S, const CasWalker& cw, const double
 
 // neighbours [i0, i1) of the class-block enumeration, reach-back per lane
 template <int W, int MODE, class C>
-__device__ __noinline__ LaneAcc2 fois_unit(const SysDev& S, const WarpSh& sh, const unsigned long long (&n)[2][W], long long ln,
+__device__ __noinline__ LaneAcc2 fois_unit(const SysDev& S, const WarpSh& sh, const double* __restrict__ gops,
+                          const unsigned long long (&n)[2][W], long long ln,
                           double c0, double inv_psin, float inv_psin_f, unsigned long long self_key, double phi_self,
                           int i0, int i1, LaneAcc2 acc, unsigned step, unsigned wid, int lane, mrq_neighbour* nbout,
                           long long nbase, long long max_nb, C& ctr) {
@@ -615,8 +616,11 @@ __device__ __noinline__ LaneAcc2 fois_unit(const SysDev& S, const WarpSh& sh, co
                 flip_reg<W>(m, s4, a2 - s4 * S.n);
             }
         }
-        const double hnm =
-            (kind == 0) ? single_elem<W>(S, n, r1, a1, ctr) : hb_screen(S, double_elem<W>(S, n, r1, r2, a1, a2, ctr));
+        double hnm;
+        if (kind != 0) hnm = hb_screen(S, double_elem<W>(S, n, r1, r2, a1, a2, ctr));
+        else if (gops != nullptr && in_walker_block(S, r1, a1))
+            hnm = single_from_walker<W>(S, SglFromWalker{gops, 0, 0, 0, 0, 0}, n, r1, a1, ctr);
+        else hnm = single_elem<W>(S, n, r1, a1, ctr);
         int hm, pm;
         const long long lm = det_label<W>(S, m, hm, pm);
         double om, psim;
@@ -625,7 +629,8 @@ __device__ __noinline__ LaneAcc2 fois_unit(const SysDev& S, const WarpSh& sh, co
             om = hash_lookup(S, hash_key(S, active_bits<W>(S, m[0]), active_bits<W>(S, m[1])), ctr);
             psim = c0 * om;
         } else {
-            om = reach_back<W>(S, m, ctr, self_key, hnm * phi_self);
+            om = reach_back<W>(S, m, ctr, self_key, hnm * phi_self,
+                               SglFromWalker{gops, kind == 0 ? 1 : 2, r1, r2, a1, a2});
             ctr.g();
             psim = __ldg(S.c + lm) * om;
         }
@@ -697,7 +702,40 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
         cw.phin = psin / c0;
         cw.inv_psin = inv_psin;
         cw.inv_psin_f = inv_psin_f;
-        // the walker's single-excitation operator, by the whole block
+        units = S.unit_off[8];
+        if (threadIdx.x == 0) cs.cw = cw;
+    }
+    // the walker's single-excitation operator G_yx(n) = h_yx + sum_{j in n} [(yx|jj) - delta (yj|jx)]
+    // for y in core + active, x in active + virtual (not both active), by the whole block: the
+    // full-core operator hc, n's active electrons, minus n's core holes, plus its virtual electrons
+    if (psin != 0.0) {
+        const unsigned ao0 = active_bits<W>(S, n[0]), ao1 = active_bits<W>(S, n[1]);
+        const unsigned long long AOn = (unsigned long long)ao0 | ((unsigned long long)ao1 << 32);
+        int nh = 0, np = 0, hso[2] = {0, 0}, pso[2] = {0, 0};
+        if (!cas) {
+#pragma unroll
+            for (int sg = 0; sg < 2; sg++) {
+                unsigned long long hm = ~(sg ? n[1][0] : n[0][0]) & S.mcore[0];
+                while (hm) {
+                    const int i = __ffsll(hm) - 1;
+                    hm &= hm - 1;
+                    if (nh == 0) hso[0] = sg * S.n + i;
+                    else hso[1] = sg * S.n + i;
+                    nh++;
+                }
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    unsigned long long pm = (sg ? n[1][w] : n[0][w]) & S.mvirt[w];
+                    while (pm) {
+                        const int a = 64 * w + __ffsll(pm) - 1;
+                        pm &= pm - 1;
+                        if (np == 0) pso[0] = sg * S.n + a;
+                        else pso[1] = sg * S.n + a;
+                        np++;
+                    }
+                }
+            }
+        }
         const int blk = S.nca * S.nav;
         for (int t = threadIdx.x; t < 2 * blk; t += blockDim.x) {
             const int sg = t >= blk, rem = t - sg * blk;
@@ -705,7 +743,7 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
             if (y >= S.nc && xo < S.na) continue;
             ctr.g();
             double v = __ldg(S.hc + y * S.n + x);
-            unsigned long long bits = cw.AOn;
+            unsigned long long bits = AOn;
             while (bits) {
                 const int b = __ffsll(bits) - 1;
                 bits &= bits - 1;
@@ -717,10 +755,19 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
                     ctr.g();
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                if (k < nh) {
+                    v -= g_corr(S, sg, x, y, hso[k]);
+                    ctr.g(2);
+                }
+                if (k < np) {
+                    v += g_corr(S, sg, x, y, pso[k]);
+                    ctr.g(2);
+                }
+            }
             gops[t] = v;
         }
-        units = S.unit_off[8];
-        if (threadIdx.x == 0) cs.cw = cw;
     }
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -770,8 +817,8 @@ __device__ StepOut block_local(CtaSh& cs, unsigned char* lists, const unsigned l
                 }
             } else {
                 const int i0 = u * MRQ_FOIS_CH, i1 = min(total_fois, i0 + MRQ_FOIS_CH);
-                acc = fois_unit<W, MODE>(S, cs.L, nsh, ln, c0, inv_psin, inv_psin_f, self_key, phi_self, i0, i1, acc,
-                                         step, wid, lane, nbout, 0, max_nb, ctr);
+                acc = fois_unit<W, MODE>(S, cs.L, psin != 0.0 ? gops : nullptr, nsh, ln, c0, inv_psin, inv_psin_f,
+                                         self_key, phi_self, i0, i1, acc, step, wid, lane, nbout, 0, max_nb, ctr);
                 ctr.mark(7);
             }
         }
