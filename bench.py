@@ -447,7 +447,8 @@ def measure_batched(n_systems: int, total_walkers: int, R: int, steps: int, warm
     6-max_act, references of 400 to 5e5 determinants, walkers proportional to the reference size)
     run three ways with the same reporting interval of R walker steps (one finalize per system):
     plain (one system per launch, one after the other), batched (every system in one launch per
-    determinant width) and batched with the autotuned launch configuration and CUDA-graph replay."""
+    determinant width and occupancy class) and batched with the autotuned launch configuration and
+    CUDA-graph replay."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     import synthetic as S
     specs, walkers = S.batch_specs(n_systems, total_walkers=total_walkers, max_act=max_act)

@@ -219,9 +219,10 @@ int mrq_finalize_noalloc(mrq_ctx* ctx, mrq_result* out);
 
 /*
  * Batched walk: advance the walkers of n contexts (independent systems, each initialised with
- * mrq_walkers_init) by n_steps in one walk launch per determinant width, so that many small
- * systems fill the GPU together (the paper runs each system on its own; walkers are independent
- * Markov chains, Sec. II B).  Walker ids, seeds and accumulators stay per context, so every
+ * mrq_walkers_init) by n_steps in one walk launch per determinant width and occupancy class (the
+ * walk blocks per SM a system's shared memory allows, so that small systems are not held to the
+ * occupancy of the largest), so that many small systems fill the GPU together (the paper runs each
+ * system on its own; walkers are independent Markov chains, Sec. II B).  Walker ids, seeds and accumulators stay per context, so every
  * trajectory is the same as when its context advances alone.  All contexts must be on one device;
  * the launch uses ctxs[0]'s stream after waiting for every context's stream, and returns after it
  * completes.  The walk time is reported by mrq_finalize on ctxs[0] only.

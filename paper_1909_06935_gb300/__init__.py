@@ -459,7 +459,8 @@ def _ctx_array(ctxs):
 
 
 def batch_advance(ctxs, n_steps: int):
-    """Advance the walkers of several contexts together (one walk launch per determinant width)."""
+    """Advance the walkers of several contexts together (one walk launch per determinant width and
+    occupancy class)."""
     lib = load_library()
     rc = lib.mrq_batch_advance(C.cast(_ctx_array(ctxs), C.c_void_p), len(ctxs), n_steps)
     if rc:

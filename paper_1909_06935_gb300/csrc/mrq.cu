@@ -1047,8 +1047,10 @@ struct mrq_ctx {
                    k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap && gstride == o.gstride;
         }
     };
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // per determinant width
-    GraphKey gkey[2];
+    // per determinant width and occupancy class (resident walk blocks per SM, 1-4) of a batch
+    cudaGraphExec_t gexec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    GraphKey gkey[8];
+    int smem_sm = 0, smem_rsv = 0;   // shared memory per SM and reserved per block (bytes)
     long long graph_replays = 0;
     long long* d_nbpre = nullptr;    // debug records: neighbour offsets of a determinant's units
     long long nbpre_cap = 0;
@@ -1440,6 +1442,11 @@ int mrq_create(mrq_ctx** out, int device) {
     }
     ctx->own_stream = true;
     cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (cudaDeviceGetAttribute(&ctx->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess) {
+        mrq_destroy(ctx);
+        return MRQ_CUDA_ERROR;
+    }
     // set-up of the allocation-free finalize: the device address of the fixed scratch array,
     // looked up once per device with that device current (host code cannot use the symbol itself)
     noalloc_scratch_address(device);
@@ -1467,7 +1474,7 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_tune);
     dfree(ctx->d_tptr);
     dfree(ctx->d_nbpre);
-    for (int w = 0; w < 2; w++)
+    for (int w = 0; w < 8; w++)
         if (ctx->gexec[w]) cudaGraphExecDestroy(ctx->gexec[w]);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -2020,8 +2027,19 @@ static int batch_check(mrq_ctx* const* ctxs, int n) {
 
 // the batch's systems of determinant width W: device tables in the lead context, walker arrays
 // from `walkers` (the contexts' own, or the tuner's scratch copies)
+// occupancy class of a system in a batch launch: the walk blocks per SM (1-4) its own shared
+// memory allows; a batch launches each class separately, so that small systems are not held to the
+// occupancy of the largest one
+static int batch_class(const mrq_ctx* lead, const mrq_ctx* c, int nw) {
+    if (c->W != 1) return 2;
+    const long long per = (long long)cta_smem_bytes(std::min(nw, MRQ_MAXNW), c->hsys.cand_cap, c->hsys.gstride) +
+                          lead->smem_rsv;
+    const long long b = per > 0 ? (long long)lead->smem_sm / per : 1;
+    return (int)std::max(1LL, std::min(4LL, b));
+}
+
 static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walkers, WalkSet& ws, int& cap,
-                        int& gstride) {
+                        int& gstride, int cls = 0, int nw = MRQ_MAXNW) {
     mrq_ctx* ctx = ctxs[0];
     if (n > ctx->bcap) {
         dfree(ctx->d_bsys);
@@ -2038,6 +2056,7 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
     cap = 1;
     for (int i = 0; i < n; i++) {
         if (ctxs[i]->W != W) continue;
+        if (cls > 0 && batch_class(ctx, ctxs[i], nw) != cls) continue;
         sys.push_back(ctxs[i]->hsys);
         wp.push_back(walkers[i]);
         off.push_back(off.back() + ctxs[i]->nwalk);
@@ -2058,7 +2077,8 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
 // n_steps steps of one width's walk set: launches of `spl` steps (the reporting interval), each
 // one sort + one walk, replayed from a CUDA graph when the lead context asks for it
 static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstride, int64_t n_steps, int wpb,
-                     int64_t spl, int accumulate, bool graph) {
+                     int64_t spl, int accumulate, bool graph, int slot = -1) {
+    if (slot < 0) slot = W - 1;
     WalkLaunch L;
     L.wpb = wpb;
     L.accumulate = accumulate;
@@ -2080,8 +2100,8 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstrid
         key.spl = (int)spl;
         key.cap = cap;
         key.gstride = gstride;
-        cudaGraphExec_t& ex = ctx->gexec[W - 1];
-        if (!ex || !(ctx->gkey[W - 1] == key)) {
+        cudaGraphExec_t& ex = ctx->gexec[slot];
+        if (!ex || !(ctx->gkey[slot] == key)) {
             if (ex) CK(cudaGraphExecDestroy(ex));
             ex = nullptr;
             CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -2099,7 +2119,7 @@ static int batch_run(mrq_ctx* ctx, int W, const WalkSet& ws, int cap, int gstrid
                 ex = nullptr;
                 return fail(ctx, MRQ_CUDA_ERROR, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
             }
-            ctx->gkey[W - 1] = key;
+            ctx->gkey[slot] = key;
         }
         for (int64_t i = 0; i < nfull; i++) CK(cudaGraphLaunch(ex, ctx->stream));
         ctx->graph_replays += nfull;
@@ -2124,12 +2144,17 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
     for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
     std::vector<Walker*> own(n);
     for (int i = 0; i < n; i++) own[i] = ctxs[i]->d_walk;
-    // one launch sequence per determinant width
-    for (int W = 1; W <= 2; W++) {
+    // one launch sequence per determinant width and occupancy class
+    for (int slot = 0; slot < 8; slot++) {
+        const int W = 1 + slot / 4, cls = 4 - slot % 4;
+        int nw = lead->wpb;
+        if (nw <= 0)
+            for (int i = 0; i < n; i++)
+                if (ctxs[i]->W == W) nw = std::max(nw, auto_warps(ctxs[i]->hsys));
         WalkSet ws;
         int cap = 1;
         int gstride = 0;
-        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap, gstride)) return r;
+        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap, gstride, cls, nw)) return r;
         if (ws.nsys == 0) continue;
         const size_t q = (size_t)ctx->launches * 2;
         while (ctx->evs.size() < q + 2) {
@@ -2138,15 +2163,11 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
             ctx->evs.push_back(ev);
         }
         CK(cudaEventRecord(ctx->evs[q], ctx->stream));
-        int nw = lead->wpb;
-        if (nw <= 0)
-            for (int i = 0; i < n; i++)
-                if (ctxs[i]->W == W) nw = std::max(nw, auto_warps(ctxs[i]->hsys));
-        if (int r = batch_run(ctx, W, ws, cap, gstride, n_steps, nw, lead->spl, 1, lead->use_graph != 0))
+        if (int r = batch_run(ctx, W, ws, cap, gstride, n_steps, nw, lead->spl, 1, lead->use_graph != 0, slot))
             return r;
         CK(cudaEventRecord(ctx->evs[q + 1], ctx->stream));
         ctx->launches++;
-        if (int r_ = sync_stream(ctx)) return r_;   // the tables are reused by the next width
+        if (int r_ = sync_stream(ctx)) return r_;   // the tables are reused by the next launch
     }
     for (int i = 0; i < n; i++) ctxs[i]->total_steps += n_steps * ctxs[i]->nwalk;
     return 0;
@@ -2207,13 +2228,14 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
         for (int rep = 0; rep < (pass < 0 ? 1 : reps); rep++) {
             if (int r = restore()) return r;
             CK(cudaEventRecord(ctx->ev0, ctx->stream));
-            for (int W = 1; W <= 2; W++) {
+            for (int slot = 0; slot < 8; slot++) {
+                const int W = 1 + slot / 4, cls = 4 - slot % 4;
                 WalkSet ws;
                 int cap = 1;
                 int gstride = 0;
-                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap, gstride)) return r;
+                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap, gstride, cls, wpb)) return r;
                 if (ws.nsys == 0) continue;
-                if (int r = batch_run(ctx, W, ws, cap, gstride, trial_steps, wpb, spl, 0, false)) return r;
+                if (int r = batch_run(ctx, W, ws, cap, gstride, trial_steps, wpb, spl, 0, false, slot)) return r;
                 if (int r_ = sync_stream(ctx)) return r_;
             }
             CK(cudaEventRecord(ctx->ev1, ctx->stream));
