@@ -186,6 +186,46 @@ def n_labels(n_core: int, n_virt: int) -> int:
     return nh * npart
 
 
+def reblock(x, min_blocks: int = 16):
+    """Flyvbjerg-Petersen blocking analysis of a correlated time series (the cross-check of the
+    jackknife error bars over walker groups): at level k the series is averaged in pairs k times,
+    and the standard error of the mean is estimated as if the blocks were independent, with its own
+    uncertainty se / sqrt(2 (n_k - 1)).  The estimate grows with k until the blocks are longer than
+    the correlation time, then stays on a plateau; the returned `sigma` is the first level (with at
+    least min_blocks blocks) whose estimate the next level does not exceed by more than this
+    uncertainty, else the largest estimate among the levels with at least min_blocks blocks.
+    Returns dict(levels=[(n_blocks, se, d_se), ...], sigma, level)."""
+    x = np.asarray(x, dtype=np.float64).ravel()
+    levels = []
+    while len(x) >= 2:
+        n = len(x)
+        se = float(np.sqrt(np.mean((x - x.mean()) ** 2) / (n - 1)))
+        levels.append((n, se, se / np.sqrt(2.0 * (n - 1))))
+        if n % 2:
+            x = x[:-1]
+        x = 0.5 * (x[0::2] + x[1::2])
+    ok = [k for k, lv in enumerate(levels) if lv[0] >= min_blocks]
+    if not ok:
+        return dict(levels=levels, sigma=float("nan"), level=-1)
+    for k in ok[:-1]:
+        if levels[k + 1][1] <= levels[k][1] + levels[k][2]:
+            return dict(levels=levels, sigma=levels[k][1], level=k)
+    k = max(ok, key=lambda i: levels[i][1])
+    return dict(levels=levels, sigma=levels[k][1], level=k)
+
+
+def reblock_ratio(num, den, min_blocks: int = 16):
+    """Blocking analysis of R = sum(num) / sum(den) from per-block sums (e.g. E_var = sum w E_L /
+    sum w, a0^2 = c0^2 sum w delta_CAS / sum w): the linearised series (num_b - R den_b) / mean(den)
+    has the error of R as the standard error of its mean.  Returns reblock()'s dict plus R."""
+    num = np.asarray(num, dtype=np.float64).ravel()
+    den = np.asarray(den, dtype=np.float64).ravel()
+    R = float(num.sum() / den.sum())
+    out = reblock((num - R * den) / den.mean(), min_blocks)
+    out["R"] = R
+    return out
+
+
 def frozen_core_coeffs(c, n_core: int, n_virt: int):
     """Sampling coefficients of the frozen-core variant (the paper's own implementation, Sec. II D):
     c_l = 0 for every label with a core hole, so that psi_s vanishes on core-excited determinants,
