@@ -30,8 +30,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "cas10_56o"
 # DRAM bytes (read + write) per walker-step of the walk kernel, from an ncu capture of one
-# steady-state launch of the current kernel (empty until the current kernel has one)
-TRAFFIC_PER_WALKER_STEP = {}
+# steady-state launch of the current kernel: dram__bytes_read.sum + dram__bytes_write.sum =
+# 183.68 MB + 6630.77 MB for 4,096 walkers on the 56-orbital workload
+TRAFFIC_PER_WALKER_STEP = {"cas10_56o": (183.676416e6 + 6630.774e6) / 4096}
 METRIC = "walker-steps/s"
 # FP64 FMA pipe of GB300: 2 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
