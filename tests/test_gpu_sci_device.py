@@ -134,3 +134,39 @@ def test_semicanonical_rotation_matches_the_host_up_to_orbital_signs():
         assert np.all(np.diff(np.diag(B)) >= 0)           # ascending, as the eigenvalues come
     assert np.allclose(info["eps"][: nc], np.diag(F)[:nc], atol=1e-10)
     assert np.allclose(info["gamma"], gamma_h, atol=1e-8)
+
+
+def test_edge_cases_of_the_string_space():
+    """A full active space (one string per spin, no opposite-spin lists), an empty one (no active
+    electrons), a request for more strings than exist (clamped), and invalid requests."""
+    import paper_1909_06935_gb300 as P
+    h1, L = S.make_integrals(2, 3, 4, 18, 3, chol_sigma=0.05)
+    for nel, nstr in ((5, 1), (2, 1), (3, 3)):
+        ctx = _ctx(2, 3, 4, nel, h1, L)
+        try:
+            r = ctx.sci_reference(50, n_seed_strings=50, tol=1e-10, max_iter=100, semicanonical=True)
+            e0 = ctx.setup_info()["e0"]
+        finally:
+            ctx.close()
+        assert r["n_strings"] == nstr and r["n_det"] == nstr * nstr
+        dets = _product_dets(r["strings"], 2, 9)
+        w = np.linalg.eigvalsh(_dense_h(_oracle(2, 3, 4, nel, h1, L, dets), dets))
+        assert abs(r["energy"] - w[0]) < 1e-9 * max(1.0, abs(w[0]))
+        assert abs(e0 - w[0]) < 1e-8 * max(1.0, abs(w[0]))
+    ctx = _ctx(2, 3, 4, 3, h1, L)
+    try:
+        for bad in (dict(n_strings=2, n_seed_strings=3), dict(n_strings=3, n_seed_strings=0),
+                    dict(n_strings=3, n_seed_strings=1, tol=0.0), dict(n_strings=3, n_seed_strings=1, max_sub=1)):
+            with pytest.raises(P.MRQError) as e:
+                ctx.sci_reference(**bad)
+            assert e.value.code == -1
+    finally:
+        ctx.close()
+    ctx = P.Context()
+    try:
+        ctx.load_hamiltonian(2, 3, 4, 3, 2, h1, S.pack_eri(L))      # open shell: Sz != 0
+        with pytest.raises(P.MRQError) as e:
+            ctx.sci_reference(3, n_seed_strings=1)
+        assert e.value.code == -1
+    finally:
+        ctx.close()
