@@ -30,8 +30,9 @@
 #define MRQ_UNIT_NB 1024      // neighbours per unit of an (X_a, Y_a) pair (pairs are cut into chunks)
 // The walk kernel is compiled for 2, 3 and 4 resident blocks of MRQ_MAXNW warps per SM (128, 80
 // and 64 registers); the runtime takes the most blocks the launch's shared memory allows.  More
-// resident warps hide more of the gathers' latency: at 56 orbitals (39 KB per block) four blocks
-// beat three and three beat two (239, 245 and 263 ms per step).
+// resident warps hide more of the gathers' latency: at 56 orbitals (45 KB per block) four blocks
+// beat three and three beat two (224, 243 and 263 ms per step); five blocks at 48 registers spill
+// too much (268 ms).
 
 // the walker block's shared state (dynamic shared memory starts with it)
 struct CasWalker {
