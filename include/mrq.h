@@ -9,7 +9,9 @@
  *
  * Conventions shared by every call:
  *  - n = n_core + n_act + n_virt spatial orbitals (n <= 128), ordered core, active, virtual;
- *    n_core <= 64, n_act <= 32.
+ *    n_core <= 64, n_act <= 32.  A walker's block keeps one reach-back candidate list per warp in
+ *    shared memory: systems whose lists are too long for eight warps run with four, two or one
+ *    (mrq_load_hamiltonian returns MRQ_TOO_LARGE only when one warp's list does not fit).
  *  - A determinant is 2W uint64 words, W = ceil(n/64): alpha occupation bits (bit p of word
  *    p/64 set when spatial orbital p holds an alpha electron), then beta.  Its sign convention
  *    is |det> = prod_{alpha p ascending} a+_p prod_{beta p ascending} a+_p |vac>.
@@ -67,8 +69,9 @@ typedef struct {
     int32_t n_groups;       /* G walker groups for jackknife errors (walker w is in group w mod G) */
     int32_t method;         /* mrq_method: informative; both estimators are always accumulated */
     double screen_tau;      /* perturbers with N_l/N_0 below this are screened out (Sec. II C) */
-    int32_t warps_per_walker;  /* 1, 2, 4 or 8 warps in each walker's thread block; 0 keeps the context's
-                                  setting (by default chosen from the system's size, see mrq_set_launch) */
+    int32_t warps_per_walker;  /* 1, 2, 4 or 8 warps in each walker's thread block (at most what the
+                                  system's candidate lists allow); 0 keeps the context's setting (by
+                                  default chosen from the system's size, see mrq_set_launch) */
     int32_t steps_per_check;   /* mrq_sample with target_sigma: steps between error checks (0: n_steps/16) */
     double target_sigma;    /* mrq_sample stops early once the jackknife sigma of E^(2) (method
                                SC_NEVPT2) or of E (SC_MRCI) is at or below this; 0 = off */

@@ -1036,6 +1036,7 @@ struct mrq_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch configuration (mrq_set_launch, mrq_tune_batch)
     int wpb = 0;                     // warps per walker block (0: chosen from the system's work units)
+    int max_nw = MRQ_MAXNW;          // most warps per walker whose candidate lists fit shared memory
     int spl = 0;                     // steps per launch (0: every advance is one launch)
     int use_graph = 0;               // batches replay one reporting interval from a CUDA graph
     struct GraphKey {
@@ -1047,9 +1048,11 @@ struct mrq_ctx {
                    k == o.k && wpb == o.wpb && spl == o.spl && cap == o.cap && gstride == o.gstride;
         }
     };
-    // per determinant width and occupancy class (resident walk blocks per SM, 1-4) of a batch
-    cudaGraphExec_t gexec[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    GraphKey gkey[8];
+    // per determinant width, warps per walker (8, 4, 2, 1) and occupancy class (resident walk blocks
+    // per SM, 4-1) of a batch launch
+    static constexpr int NSLOT = 32;
+    cudaGraphExec_t gexec[NSLOT] = {};
+    GraphKey gkey[NSLOT];
     int smem_sm = 0, smem_rsv = 0;   // shared memory per SM and reserved per block (bytes)
     long long graph_replays = 0;
     long long* d_nbpre = nullptr;    // debug records: neighbour offsets of a determinant's units
@@ -1255,7 +1258,11 @@ static int auto_warps(const SysDev& s) {
     const int u = s.unit_off[8];
     return u >= 512 ? 8 : (u >= 128 ? 4 : 2);
 }
-static int warps_of(const mrq_ctx* ctx) { return ctx->wpb > 0 ? ctx->wpb : auto_warps(ctx->hsys); }
+// warps per walker of a context's launches: the requested (or automatic) number, at most the most
+// whose per-warp candidate lists fit shared memory (large active spaces run with fewer warps)
+static int warps_of(const mrq_ctx* ctx) {
+    return std::min(ctx->wpb > 0 ? ctx->wpb : auto_warps(ctx->hsys), ctx->max_nw);
+}
 
 // nsteps walker steps of a walk set: per step, order the slots by determinant (when the slot count
 // allows a one-block sort), one block of L.wpb warps per walker slot (k_walk2), then the
@@ -1394,7 +1401,12 @@ static int walk_plan(mrq_ctx* ctx, SysDev& s) {
     s.gstride = 2 * s.nca * s.nav;
     s.cand_cap = (int)cap;
     ctx->cand_cap_full = (int)cap;
-    if (cta_smem_bytes(MRQ_MAXNW, (int)cap, s.gstride) > 227 * 1024)
+    // the most warps per walker (8, 4, 2 or 1) whose candidate lists and operator fit one block's
+    // shared memory; beyond one warp the active space is too large for the walk
+    ctx->max_nw = 0;
+    for (int nw = MRQ_MAXNW; nw >= 1 && ctx->max_nw == 0; nw >>= 1)
+        if (cta_smem_bytes(nw, (int)cap, s.gstride) <= 227 * 1024) ctx->max_nw = nw;
+    if (ctx->max_nw == 0)
         return fail(ctx, MRQ_TOO_LARGE, "active space too large for the shared-memory candidate lists");
     return 0;
 }
@@ -1474,7 +1486,7 @@ void mrq_destroy(mrq_ctx* ctx) {
     dfree(ctx->d_tune);
     dfree(ctx->d_tptr);
     dfree(ctx->d_nbpre);
-    for (int w = 0; w < 8; w++)
+    for (int w = 0; w < mrq_ctx::NSLOT; w++)
         if (ctx->gexec[w]) cudaGraphExecDestroy(ctx->gexec[w]);
     for (auto e : ctx->evs) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -2032,14 +2044,16 @@ static int batch_check(mrq_ctx* const* ctxs, int n) {
 // occupancy of the largest one
 static int batch_class(const mrq_ctx* lead, const mrq_ctx* c, int nw) {
     if (c->W != 1) return 2;
-    const long long per = (long long)cta_smem_bytes(std::min(nw, MRQ_MAXNW), c->hsys.cand_cap, c->hsys.gstride) +
+    const long long per = (long long)cta_smem_bytes(std::min(nw, c->max_nw), c->hsys.cand_cap, c->hsys.gstride) +
                           lead->smem_rsv;
     const long long b = per > 0 ? (long long)lead->smem_sm / per : 1;
     return (int)std::max(1LL, std::min(4LL, b));
 }
 
+// the systems of one batch launch: width W, warps per walker nw_eff (the requested nw, at most
+// what each system's candidate lists allow) and occupancy class cls (0: every class)
 static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walkers, WalkSet& ws, int& cap,
-                        int& gstride, int cls = 0, int nw = MRQ_MAXNW) {
+                        int& gstride, int cls = 0, int nw = MRQ_MAXNW, int nw_eff = 0) {
     mrq_ctx* ctx = ctxs[0];
     if (n > ctx->bcap) {
         dfree(ctx->d_bsys);
@@ -2056,6 +2070,7 @@ static int batch_tables(mrq_ctx* const* ctxs, int n, int W, Walker* const* walke
     cap = 1;
     for (int i = 0; i < n; i++) {
         if (ctxs[i]->W != W) continue;
+        if (nw_eff > 0 && std::min(nw, ctxs[i]->max_nw) != nw_eff) continue;
         if (cls > 0 && batch_class(ctx, ctxs[i], nw) != cls) continue;
         sys.push_back(ctxs[i]->hsys);
         wp.push_back(walkers[i]);
@@ -2144,9 +2159,9 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
     for (int i = 0; i < n; i++) CK(cudaStreamSynchronize(ctxs[i]->stream));
     std::vector<Walker*> own(n);
     for (int i = 0; i < n; i++) own[i] = ctxs[i]->d_walk;
-    // one launch sequence per determinant width and occupancy class
-    for (int slot = 0; slot < 8; slot++) {
-        const int W = 1 + slot / 4, cls = 4 - slot % 4;
+    // one launch sequence per determinant width, warps per walker and occupancy class
+    for (int slot = 0; slot < mrq_ctx::NSLOT; slot++) {
+        const int W = 1 + slot / 16, nw_eff = MRQ_MAXNW >> ((slot / 4) % 4), cls = 4 - slot % 4;
         int nw = lead->wpb;
         if (nw <= 0)
             for (int i = 0; i < n; i++)
@@ -2154,7 +2169,7 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
         WalkSet ws;
         int cap = 1;
         int gstride = 0;
-        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap, gstride, cls, nw)) return r;
+        if (int r = batch_tables(ctxs, n, W, own.data(), ws, cap, gstride, cls, nw, nw_eff)) return r;
         if (ws.nsys == 0) continue;
         const size_t q = (size_t)ctx->launches * 2;
         while (ctx->evs.size() < q + 2) {
@@ -2163,7 +2178,7 @@ int mrq_batch_advance(mrq_ctx* const* ctxs, int n, int64_t n_steps) {
             ctx->evs.push_back(ev);
         }
         CK(cudaEventRecord(ctx->evs[q], ctx->stream));
-        if (int r = batch_run(ctx, W, ws, cap, gstride, n_steps, nw, lead->spl, 1, lead->use_graph != 0, slot))
+        if (int r = batch_run(ctx, W, ws, cap, gstride, n_steps, nw_eff, lead->spl, 1, lead->use_graph != 0, slot))
             return r;
         CK(cudaEventRecord(ctx->evs[q + 1], ctx->stream));
         ctx->launches++;
@@ -2228,14 +2243,14 @@ int mrq_tune_batch(mrq_ctx* const* ctxs, int n, int64_t trial_steps, mrq_tune_re
         for (int rep = 0; rep < (pass < 0 ? 1 : reps); rep++) {
             if (int r = restore()) return r;
             CK(cudaEventRecord(ctx->ev0, ctx->stream));
-            for (int slot = 0; slot < 8; slot++) {
-                const int W = 1 + slot / 4, cls = 4 - slot % 4;
+            for (int slot = 0; slot < mrq_ctx::NSLOT; slot++) {
+                const int W = 1 + slot / 16, nw_eff = MRQ_MAXNW >> ((slot / 4) % 4), cls = 4 - slot % 4;
                 WalkSet ws;
                 int cap = 1;
                 int gstride = 0;
-                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap, gstride, cls, wpb)) return r;
+                if (int r = batch_tables(ctxs, n, W, scratch.data(), ws, cap, gstride, cls, wpb, nw_eff)) return r;
                 if (ws.nsys == 0) continue;
-                if (int r = batch_run(ctx, W, ws, cap, gstride, trial_steps, wpb, spl, 0, false, slot)) return r;
+                if (int r = batch_run(ctx, W, ws, cap, gstride, trial_steps, nw_eff, spl, 0, false, slot)) return r;
                 if (int r_ = sync_stream(ctx)) return r_;
             }
             CK(cudaEventRecord(ctx->ev1, ctx->stream));
