@@ -470,7 +470,8 @@ int mrq_set_heat_bath_cutoff(mrq_ctx* ctx, double eps);
 
 /*
  * Copy the loaded integrals back (h1: n*n doubles, eri: the 8-fold packed array; either may be
- * NULL), e.g. after mrq_sci_reference rotated them.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
+ * NULL), e.g. the semicanonical core and virtual orbitals Dyall's H_D assumes (Sec. II C) after
+ * mrq_sci_reference rotated them.  Errors: MRQ_NOT_LOADED, MRQ_CUDA_ERROR.
  */
 int mrq_read_hamiltonian(mrq_ctx* ctx, double* h1, double* eri);
 
