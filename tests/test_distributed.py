@@ -99,3 +99,60 @@ def test_groups_per_rank_keeps_the_union_within_64():
     for w in (1, 2, 3, 4, 5, 8, 16, 64, 100):
         assert 1 <= bench.groups_per_rank(w) <= 16
         assert w * bench.groups_per_rank(w) <= 64 or bench.groups_per_rank(w) == 1
+
+
+class _FakeCtx:
+    """Stands in for a device context: fixed per-group sums, and it records what rank 0 loads."""
+
+    def __init__(self, rank, G, L):
+        import numpy as np
+        rng = np.random.default_rng(100 + rank)
+        self.acc = dict(N=rng.random((G, L)), U=rng.random((G, L)), W=rng.random(G), E=rng.random(G),
+                        type_steps=np.full(9, rank + 1, np.int64))
+        self.grad = (rng.random((G, L)), rng.random((G, L)))
+        self.loaded = None
+
+    def accumulators(self, G):
+        return {k: v.copy() for k, v in self.acc.items()}
+
+    def gradient_sums(self, G):
+        return self.grad
+
+    def load_accumulators(self, acc, total_steps=0):
+        self.loaded = (acc, total_steps)
+
+    def finalize(self):
+        a, _ = self.loaded
+        return dict(e2=float(a["E"].sum()), e2_sigma=1.0, e_var=float(a["W"].sum()), e_var_sigma=2.0)
+
+
+def _combine_worker(rank, world, port, out):
+    import numpy as np
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    G = bench.groups_per_rank(world)
+    ctx = _FakeCtx(rank, G, 5)
+    res = bench.combine_ranks(ctx, G, world, rank, total_steps=1000 * (rank + 1))
+    if rank == 0:
+        acc, steps = ctx.loaded
+        others = [_FakeCtx(r, G, 5) for r in range(world)]
+        ok = all(np.array_equal(acc["N"][r * G:(r + 1) * G], others[r].acc["N"]) and
+                 np.array_equal(acc["A"][r * G:(r + 1) * G], others[r].grad[0]) for r in range(world))
+        out[0] = (res, steps, ok, int(acc["type_steps"][0]))
+    else:
+        out[rank] = (res,)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_combine_ranks_loads_the_union_on_rank_zero_only():
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_combine_worker, args=(3, port, out), nprocs=3, start_method="spawn", join=True)
+    res, steps, ok, t0 = out[0]
+    import bench
+    assert ok and steps == 1000 + 2000 + 3000 and t0 == 1 + 2 + 3
+    assert res["groups"] == 3 * bench.groups_per_rank(3) and res["walker_steps"] == 6000
+    assert out[1] == (None,) and out[2] == (None,)
